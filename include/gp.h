@@ -1,0 +1,193 @@
+/*
+ * gp.h -- C ABI of the GB300 (sm_103a) split-step Crank-Nicolson solver for the
+ * time-dependent Gross-Pitaevskii (GP) equation in a fully anisotropic 3D
+ * harmonic trap.
+ *
+ * Paper: "OpenMP Fortran and C programs for solving the time-dependent
+ * Gross-Pitaevskii equation in an anisotropic trap", program summary:
+ *   - Nature of problem: GP equation for a condensate with contact interaction in a
+ *     fully anisotropic 3D harmonic trap.
+ *   - Solution method: split-step Crank-Nicolson (SSCN) discretisation in space and
+ *     time, propagation over small steps in imaginary time (stationary state) or
+ *     real time (dynamics).
+ *   - Summary of revisions: inputs are the number of atoms, the scattering length
+ *     and the oscillator length, from which the dimensionless nonlinearity is
+ *     computed; outputs are energy, chemical potential, rms sizes, the density and
+ *     the integrated 1D / 2D densities (Eq. 1); the real-time run starts from the
+ *     imaginary-time state and multiplies the nonlinearity by a factor (quench).
+ *
+ * Equation and discretisation (the paper names the method but prints neither; the
+ * textbook forms are used):
+ *   i dpsi/dt = [-(1/2) Lap + V + g |psi|^2] psi,
+ *   V = (gamma^2 x^2 + nu^2 y^2 + lambda^2 z^2) / 2,   g = 4 pi N a_s / l_osc.
+ *   Grid x_i = (i - (nx-1)/2) dx, i = 0..nx-1 (box centred on the origin), same for
+ *   y and z; psi = 0 on the ghost points just outside the box.
+ *   One step, tau = dt (imaginary time, real field) or i dt (real time, complex field):
+ *     1. psi <- psi exp(-tau (V + g |psi|^2))                     (pointwise)
+ *     2. per axis x, y, z, on every grid line, one Crank-Nicolson solve
+ *        (1+2a) u_j - a (u_{j-1}+u_{j+1}) = (1-2a) v_j + a (v_{j-1}+v_{j+1}),
+ *        a = tau / (4 h^2), by a Thomas recurrence with precomputed coefficients
+ *     3. imaginary time: psi <- psi / sqrt(sum |psi|^2 dV)           (renormalise)
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative GP_ERR_* code; nothing is thrown.
+ *   - Host pointers are owned by the caller and are only used during the call.
+ *   - Device memory is owned by the library (gp_create) or by the caller
+ *     (gp_create_on); the solver never frees a caller's buffer.
+ *   - Work is queued on the stream given at creation (NULL: the legacy default
+ *     stream).  gp_step_* return as soon as the work is queued; gp_sync,
+ *     gp_observables, gp_get_psi and the density calls wait for it, and report
+ *     GP_ERR_NONFINITE when a step produced a non-finite or zero norm and
+ *     GP_ERR_TIMEOUT when a kernel's bounded wait on its own copies ran out.
+ *   - Host-side arrays use the layout psi[k][j][i] (x fastest, index
+ *     (k*ny + j)*nx + i), FP64, complex values interleaved (re, im), whatever the
+ *     storage precision on the device.
+ *   - A solver is not thread-safe; distinct solvers are independent.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GP_OK 0
+#define GP_ERR_ARG (-1)       /* invalid argument or unsupported size          */
+#define GP_ERR_NOMEM (-2)     /* device allocation failed or buffer too small  */
+#define GP_ERR_CUDA (-3)      /* a CUDA call failed (see gp_last_error)        */
+#define GP_ERR_NONFINITE (-4) /* the norm became non-finite or zero            */
+#define GP_ERR_TIMEOUT (-5)   /* a kernel's bounded wait gave up               */
+#define GP_ERR_STATE (-6)     /* call not valid in the solver's current mode   */
+
+/* Storage precision of the field.  FP64: double / complex double, all arithmetic
+ * in FP64.  FP32: float / complex float storage and sweeps; elimination
+ * coefficients computed in FP64 and rounded once; norm and observables
+ * accumulated in FP64.                                                           */
+typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_prec;
+
+/* Problem definition ("Summary of revisions": physical inputs, trap anisotropy).
+ *   nx, ny, nz     grid points per axis, each 3..2048
+ *   dx, dy, dz     grid spacings (> 0), dimensionless (units of the x oscillator length)
+ *   dt             time step (> 0)
+ *   gamma, nu, lambda  trap frequencies relative to the x trap (> 0)
+ *   use_physical   0: take g as given; 1: g = 4 pi natoms a_s / l_osc, with a_s and
+ *                  l_osc in the same length unit
+ *   prec           gp_prec                                                       */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  double dt;
+  double gamma, nu, lambda;
+  int use_physical;
+  double g;
+  double natoms, a_s, l_osc;
+  int prec;
+} gp_params;
+
+/* Observables ("Summary of revisions": energy, chemical potential, rms sizes).
+ *   norm   = sum |psi|^2 dV
+ *   ekin   = <psi| -(1/2) Lap_h |psi> dV   (3-point Laplacian, zero ghosts: the
+ *            operator of the CN substep)
+ *   epot   = sum V |psi|^2 dV,   eint = (g/2) sum |psi|^4 dV
+ *   energy = ekin + epot + eint,  mu = ekin + epot + 2 eint
+ *   rms_a  = sqrt(sum a^2 |psi|^2 dV / norm), rms_r = sqrt(rms_x^2+rms_y^2+rms_z^2)
+ * energy and mu are the per-atom values for a unit-norm state, which imaginary
+ * time enforces and real time conserves.                                         */
+typedef struct {
+  double norm, mu, energy, ekin, epot, eint, rms_x, rms_y, rms_z, rms_r;
+} gp_obs;
+
+typedef struct gp_solver gp_solver;
+
+/* Device bytes that gp_create_on needs for these parameters (host only, no CUDA
+ * call).  Returns GP_ERR_ARG for invalid parameters.                             */
+int gp_workspace_bytes(const gp_params* p, size_t* bytes);
+
+/* Validate p, compute g, the Crank-Nicolson elimination coefficients (FP64) and
+ * the trap tables, allocate the device state with cudaMalloc on the current
+ * device and bind `stream` (a cudaStream_t, or NULL).  The field starts at zero.
+ * *out receives the solver, or NULL on error (then gp_last_error(NULL) explains). */
+int gp_create(const gp_params* p, void* stream, gp_solver** out);
+
+/* Same, inside a caller-owned device buffer of `bytes` >= gp_workspace_bytes,
+ * 256-byte aligned, that must outlive the solver.                                */
+int gp_create_on(const gp_params* p, void* dev_buf, size_t bytes, void* stream,
+                 gp_solver** out);
+
+/* Wait for queued work, free library-owned memory and the solver.  NULL is a no-op. */
+void gp_destroy(gp_solver* s);
+
+/* Real field exp(-(wx x^2 + wy y^2 + wz z^2) / 2) normalised on the grid; with
+ * (wx, wy, wz) = (gamma, nu, lambda) it is the g = 0 trap ground state.
+ * Puts the solver in imaginary-time (real field) mode.                           */
+int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz);
+
+/* Copy a host field in (nx*ny*nz doubles, or 2*nx*ny*nz interleaved when
+ * is_complex) and set the mode to real field / complex field accordingly.  The
+ * field is taken as given (not renormalised).                                    */
+int gp_set_psi(gp_solver* s, const double* host, int is_complex);
+
+/* Copy the current (normalised) field out.  as_complex = 1 always works (a real
+ * field gets zero imaginary parts); as_complex = 0 on a complex field returns
+ * GP_ERR_STATE.  Synchronises.                                                   */
+int gp_get_psi(gp_solver* s, double* host, int as_complex);
+
+/* nsteps imaginary-time SSCN steps on the real field, each renormalised to unit
+ * norm.  GP_ERR_STATE on a complex field.  Asynchronous.                         */
+int gp_step_imag(gp_solver* s, long nsteps);
+
+/* nsteps real-time SSCN steps on the complex field.  On a real field the field is
+ * first promoted to complex (imaginary parts zero): the imaginary-to-real-time
+ * hand-off of the paper's real-time programs.  Asynchronous.                     */
+int gp_step_real(gp_solver* s, long nsteps);
+
+/* Replace the nonlinearity g (the paper's quench: the real-time run multiplies g
+ * by a factor).  Takes effect for the next step.                                 */
+int gp_set_g(gp_solver* s, double g);
+
+/* Current g (after the physical-units conversion and any gp_set_g). */
+int gp_get_g(const gp_solver* s, double* g);
+
+/* One FP64 pass over the field; synchronises; *out receives the observables. */
+int gp_observables(gp_solver* s, gp_obs* out);
+
+/* Integrated densities, Eq. 1 and its 3D analogues, FP64, synchronous.
+ *   density1d: axis 0: out[i] = sum_{j,k} |psi|^2 dy dz   (out has nx entries)
+ *              axis 1: out[j] = sum_{i,k} |psi|^2 dx dz   (ny entries)
+ *              axis 2: out[k] = sum_{i,j} |psi|^2 dx dy   (nz entries)
+ *   density2d: plane 0 (xy): out[j*nx+i] = sum_k |psi|^2 dz
+ *              plane 1 (xz): out[k*nx+i] = sum_j |psi|^2 dy
+ *              plane 2 (yz): out[k*ny+j] = sum_i |psi|^2 dx                        */
+int gp_density1d(gp_solver* s, int axis, double* out);
+int gp_density2d(gp_solver* s, int plane, double* out);
+
+/* Wait for all queued work and report a status the kernels flagged since the last
+ * check (GP_ERR_NONFINITE, GP_ERR_TIMEOUT), clearing it.                         */
+int gp_sync(gp_solver* s);
+
+/* Per-sweep timing.  While enabled, every x / y / z sweep launch is bracketed by
+ * CUDA events on the solver's stream.  gp_get_timing synchronises, adds the
+ * elapsed milliseconds of the launches since the last read into ms[0..2] (x, y, z
+ * sweep) and their counts into launches[0..2], then clears them.                 */
+int gp_set_timing(gp_solver* s, int enable);
+int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]);
+
+/* Layout facts of a solver, for tests and tools:
+ *   info[0] field pitch along x in elements, info[1] 1 if the field is complex,
+ *   info[2..4] lines per CTA tile of the x / y / z sweeps,
+ *   info[5] device bytes in use.                                                 */
+int gp_get_info(const gp_solver* s, long long info[6]);
+
+/* Last error message of s, or of the calling thread's last failed gp_create /
+ * gp_create_on when s is NULL.  Never NULL.                                      */
+const char* gp_last_error(const gp_solver* s);
+
+/* Static text for a GP_* code. */
+const char* gp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

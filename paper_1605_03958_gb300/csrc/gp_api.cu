@@ -1,0 +1,801 @@
+// gp_api.cu -- host runtime behind include/gp.h: parameter checks, the physical-units
+// nonlinearity, FP64 Crank-Nicolson elimination coefficients and trap tables, the
+// device memory layout, TMA descriptors, launch sequencing of the SSCN step, status
+// checks and per-sweep event timing.
+//
+// Paper: program summary ("Solution method": split-step Crank-Nicolson, imaginary
+// and real time; "Summary of revisions": physical inputs N, a_s, l_osc turned into
+// the dimensionless nonlinearity, energy / chemical potential / rms / integrated
+// density outputs, quench by a factor on g, imaginary-to-real-time hand-off).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gp.h"
+#include "gp_internal.h"
+
+using gpk::FieldParams;
+using gpk::SweepParams;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr size_t kAlign = 256;
+constexpr size_t kFastTileBytes = 100 * 1024;   // preferred tile: >= 2 blocks per SM
+constexpr size_t kMaxTileBytes = 226 * 1024;    // opt-in shared memory per block, minus slack
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Geometry of one sweep in one mode (0: real field, 1: complex field).
+struct SweepGeom {
+  int lines = 0;      // lines per tile
+  int box = 0;        // TMA box length along the line (y / z) -- x: unused
+  int nbox = 0;
+  size_t smem = 0;    // dynamic shared memory bytes of one block
+};
+
+struct Layout {
+  size_t rbytes = 8;               // bytes of one real value (8 FP64, 4 FP32)
+  int pitch[2] = {0, 0};           // row pitch in elements, per mode
+  size_t field_bytes = 0;
+  size_t off_field = 0, off_staging = 0, off_coef = 0, off_vtab = 0, off_otab = 0;
+  size_t off_partials = 0, off_scalars = 0, total = 0;
+  size_t coef_off[2][3][2] = {};   // [mode][axis][A/B] byte offset from off_coef
+  size_t npartials = 0;
+  SweepGeom geom[2][3];
+  long long ntiles_z[2] = {0, 0};
+  int tiles_x[2][3] = {};
+};
+
+// Largest power-of-two line count (<= 32) whose tile fits `budget`; for TMA tiles the
+// tile's inner extent must be a multiple of 16 bytes.
+int choose_lines(size_t line_bytes, size_t elem_bytes, bool tma_inner, size_t budget) {
+  for (int w = 32; w >= 1; w >>= 1) {
+    if (tma_inner && ((size_t)w * elem_bytes) % 16 != 0) return 0;
+    if ((size_t)w * line_bytes + 64 <= budget) return w;
+  }
+  return 0;
+}
+
+const char* check_params(const gp_params* p) {
+  if (!p) return "params is NULL";
+  const int n[3] = {p->nx, p->ny, p->nz};
+  for (int a = 0; a < 3; ++a)
+    if (n[a] < 3 || n[a] > gpk::kMaxExtent) return "grid extents must be within 3..2048";
+  const double h[3] = {p->dx, p->dy, p->dz};
+  for (int a = 0; a < 3; ++a)
+    if (!(h[a] > 0.0) || !std::isfinite(h[a])) return "grid spacings must be finite and > 0";
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be finite and > 0";
+  if (!(p->gamma > 0.0) || !(p->nu > 0.0) || !(p->lambda > 0.0) || !std::isfinite(p->gamma) ||
+      !std::isfinite(p->nu) || !std::isfinite(p->lambda))
+    return "trap ratios gamma, nu, lambda must be finite and > 0";
+  if (p->use_physical != 0 && p->use_physical != 1) return "use_physical must be 0 or 1";
+  if (p->use_physical) {
+    if (!std::isfinite(p->natoms) || !std::isfinite(p->a_s) || !(p->l_osc > 0.0) ||
+        !std::isfinite(p->l_osc))
+      return "physical inputs need finite natoms, a_s and l_osc > 0";
+  } else if (!std::isfinite(p->g)) {
+    return "g must be finite";
+  }
+  if (p->prec != GP_F64 && p->prec != GP_F32) return "prec must be GP_F64 or GP_F32";
+  return nullptr;
+}
+
+// g = 4 pi N a_s / l_osc, or g as given.
+double nonlinearity(const gp_params* p) {
+  return p->use_physical ? 4.0 * kPi * p->natoms * p->a_s / p->l_osc : p->g;
+}
+
+const char* compute_layout(const gp_params* p, Layout* L) {
+  L->rbytes = p->prec == GP_F64 ? 8 : 4;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  const size_t N = (size_t)p->nx * p->ny * p->nz;
+  for (int m = 0; m < 2; ++m) {
+    const size_t eb = L->rbytes * (m + 1);          // element bytes
+    const size_t q = 16 / eb > 0 ? 16 / eb : 1;     // pitch multiple: rows start 16-byte aligned
+    L->pitch[m] = (int)align_up((size_t)p->nx, q);
+  }
+  const size_t rows = (size_t)p->ny * p->nz;
+  L->field_bytes = std::max((size_t)L->pitch[0] * L->rbytes, (size_t)L->pitch[1] * 2 * L->rbytes) * rows;
+
+  for (int m = 0; m < 2; ++m) {
+    const size_t eb = L->rbytes * (m + 1);
+    // x sweep: tile = lines x pitch, contiguous
+    {
+      const size_t line = (size_t)L->pitch[m] * eb;
+      int w = choose_lines(line, eb, false, kFastTileBytes);
+      if (!w) w = choose_lines(line, eb, false, kMaxTileBytes);
+      if (!w) return "x extent too large for one shared-memory row tile";
+      L->geom[m][0].lines = w;
+      L->geom[m][0].smem = (size_t)w * line + 64;
+    }
+    for (int a = 1; a < 3; ++a) {
+      SweepGeom& G = L->geom[m][a];
+      G.nbox = (n[a] + gpk::kMaxBox - 1) / gpk::kMaxBox;
+      G.box = (n[a] + G.nbox - 1) / G.nbox;
+      const size_t line = (size_t)G.nbox * G.box * eb;
+      int w = choose_lines(line, eb, true, kFastTileBytes);
+      if (!w) w = choose_lines(line, eb, true, kMaxTileBytes);
+      if (!w) return "line too long for one shared-memory tile";
+      G.lines = w;
+      G.smem = (size_t)w * line + 64;
+      L->tiles_x[m][a] = (p->nx + w - 1) / w;
+    }
+    L->ntiles_z[m] = (long long)L->tiles_x[m][2] * p->ny;
+  }
+
+  size_t off = 0;
+  L->off_field = off;
+  off = align_up(off + L->field_bytes, kAlign);
+  L->off_staging = off;
+  off = align_up(off + N * 16, kAlign);
+  L->off_coef = off;
+  size_t c = 0;
+  for (int m = 0; m < 2; ++m)
+    for (int a = 0; a < 3; ++a)
+      for (int ab = 0; ab < 2; ++ab) {
+        L->coef_off[m][a][ab] = c;
+        c = align_up(c + (size_t)n[a] * L->rbytes * (m + 1), kAlign);
+      }
+  off = align_up(off + c, kAlign);
+  L->off_vtab = off;
+  off = align_up(off + (size_t)(p->nx + p->ny + p->nz) * L->rbytes, kAlign);
+  L->off_otab = off;
+  off = align_up(off + (size_t)2 * (p->nx + p->ny + p->nz) * 8, kAlign);
+  L->off_partials = off;
+  L->npartials = std::max<size_t>((size_t)std::max(L->ntiles_z[0], L->ntiles_z[1]),
+                                  (size_t)gpk::kReduceBlocks * gpk::kObsAcc);
+  off = align_up(off + L->npartials * 8, kAlign);
+  L->off_scalars = off;
+  off = align_up(off + 512, kAlign);
+  L->total = off;
+  return nullptr;
+}
+
+// Thomas pivots of (1+2a) u_j - a (u_{j-1}+u_{j+1}): m_0 = 1/b, m_j = 1/(b - a^2 m_{j-1}),
+// b = 1 + 2a (so that cp_j = -a m_j); the sweeps use A_j = m_j (1-2a), B_j = a m_j.
+void cn_coefficients(int n, std::complex<double> a, std::vector<std::complex<double>>* A,
+                     std::vector<std::complex<double>>* B) {
+  const std::complex<double> b = 1.0 + 2.0 * a;
+  A->resize(n);
+  B->resize(n);
+  std::complex<double> cp_prev = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const std::complex<double> m = 1.0 / (j == 0 ? b : b + a * cp_prev);
+    cp_prev = -a * m;
+    (*A)[j] = m * (1.0 - 2.0 * a);
+    (*B)[j] = a * m;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+struct TimedLaunch {
+  cudaEvent_t start, stop;
+  int axis;
+};
+
+}  // namespace
+
+struct gp_solver {
+  gp_params prm;
+  Layout L;
+  double g = 0.0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool owns = false;
+  unsigned char* base = nullptr;
+  bool is_complex = false;
+  // device pointers
+  void* field = nullptr;
+  double* staging = nullptr;
+  void* vtab = nullptr;
+  double* otab = nullptr;
+  double* partials = nullptr;
+  double* scale = nullptr;
+  int* status = nullptr;
+  unsigned int* counters = nullptr;  // [0] sweeps, [1] reductions
+  double* obs = nullptr;
+  SweepParams sp[2][3];
+  CUtensorMap tmap[2][3];  // [mode][axis]; axis 0 unused (64-byte aligned type)
+  // timing
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  std::string err = "no error";
+};
+
+namespace {
+
+int fail(gp_solver* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+int cuda_fail(gp_solver* s, cudaError_t e, const char* where) {
+  return fail(s, GP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GP_CUDA(s, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+  } while (0)
+
+FieldParams field_params(gp_solver* s) {
+  FieldParams f;
+  f.psi = s->field;
+  f.nx = s->prm.nx;
+  f.ny = s->prm.ny;
+  f.nz = s->prm.nz;
+  f.pitch = s->L.pitch[s->is_complex ? 1 : 0];
+  f.scale = s->scale;
+  f.partials = s->partials;
+  f.counter = s->counters + 1;
+  f.out = s->obs;
+  f.status = s->status;
+  f.tab = s->otab;
+  f.hx = s->prm.dx;
+  f.hy = s->prm.dy;
+  f.hz = s->prm.dz;
+  f.g = s->g;
+  return f;
+}
+
+int encode_maps(gp_solver* s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(s, GP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const gp_params& p = s->prm;
+  for (int m = 0; m < 2; ++m) {
+    const int wpe = m + 1;
+    const size_t eb = s->L.rbytes * wpe;
+    const CUtensorMapDataType dt =
+        s->L.rbytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)p.nx * wpe, (cuuint64_t)p.ny, (cuuint64_t)p.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)s->L.pitch[m] * eb,
+                                   (cuuint64_t)s->L.pitch[m] * eb * p.ny};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int a = 1; a < 3; ++a) {
+      const SweepGeom& G = s->L.geom[m][a];
+      const cuuint32_t box[3] = {(cuuint32_t)(G.lines * wpe), a == 1 ? (cuuint32_t)G.box : 1u,
+                                 a == 2 ? (cuuint32_t)G.box : 1u};
+      CUresult r = enc(&s->tmap[m][a], dt, 3, s->field, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for mode %d axis %d", (int)r,
+                 m, a);
+        return fail(s, GP_ERR_CUDA, buf);
+      }
+    }
+  }
+  return GP_OK;
+}
+
+void fill_sweep_params(gp_solver* s) {
+  const gp_params& p = s->prm;
+  const int n[3] = {p.nx, p.ny, p.nz};
+  unsigned char* coef = s->base + s->L.off_coef;
+  const size_t rb = s->L.rbytes;
+  unsigned char* vt = static_cast<unsigned char*>(s->vtab);
+  for (int m = 0; m < 2; ++m)
+    for (int a = 0; a < 3; ++a) {
+      SweepParams& q = s->sp[m][a];
+      std::memset(&q, 0, sizeof q);
+      q.psi = s->field;
+      q.nx = p.nx;
+      q.ny = p.ny;
+      q.nz = p.nz;
+      q.pitch = s->L.pitch[m];
+      q.n = n[a];
+      q.lines = s->L.geom[m][a].lines;
+      q.tiles_x = s->L.tiles_x[m][a];
+      q.box = s->L.geom[m][a].box;
+      q.nbox = s->L.geom[m][a].nbox;
+      q.words_per_elem = m + 1;
+      q.A = coef + s->L.coef_off[m][a][0];
+      q.B = coef + s->L.coef_off[m][a][1];
+      q.vx = vt;
+      q.vy = vt + (size_t)p.nx * rb;
+      q.vz = vt + (size_t)(p.nx + p.ny) * rb;
+      q.dt = p.dt;
+      q.g = s->g;
+      q.scale = s->scale;
+      q.partials = s->partials;
+      q.counter = s->counters;
+      q.scale_out = s->scale;
+      q.status = s->status;
+      q.dV = p.dx * p.dy * p.dz;
+      q.ntiles = s->L.ntiles_z[m];
+    }
+}
+
+template <class T> void put(std::vector<unsigned char>& buf, size_t off, const T& v) {
+  std::memcpy(buf.data() + off, &v, sizeof(T));
+}
+
+// Host tables (coefficients in the storage precision, trap tables), one upload.
+int upload_tables(gp_solver* s) {
+  const gp_params& p = s->prm;
+  const Layout& L = s->L;
+  const int n[3] = {p.nx, p.ny, p.nz};
+  const double h[3] = {p.dx, p.dy, p.dz};
+  const double w[3] = {p.gamma, p.nu, p.lambda};
+  const bool f64 = L.rbytes == 8;
+  const size_t span = L.off_partials - L.off_coef;
+  std::vector<unsigned char> buf(span, 0);
+  auto put_real = [&](size_t off, double v) {
+    if (f64) put<double>(buf, off, v);
+    else put<float>(buf, off, (float)v);
+  };
+  for (int m = 0; m < 2; ++m)
+    for (int a = 0; a < 3; ++a) {
+      const double beta = p.dt / (4.0 * h[a] * h[a]);
+      const std::complex<double> alpha = m == 0 ? std::complex<double>(beta, 0.0)
+                                                : std::complex<double>(0.0, beta);
+      std::vector<std::complex<double>> A, B;
+      cn_coefficients(n[a], alpha, &A, &B);
+      for (int ab = 0; ab < 2; ++ab) {
+        const std::vector<std::complex<double>>& C = ab == 0 ? A : B;
+        size_t off = L.coef_off[m][a][ab];
+        for (int j = 0; j < n[a]; ++j) {
+          if (m == 0) {
+            put_real(off + j * L.rbytes, C[j].real());
+          } else {
+            put_real(off + 2 * j * L.rbytes, C[j].real());
+            put_real(off + (2 * j + 1) * L.rbytes, C[j].imag());
+          }
+        }
+      }
+    }
+  // potential tables V_a(x) = w_a^2 x^2 / 2 in storage precision, and FP64 copies + x^2
+  const size_t vt = L.off_vtab - L.off_coef, ot = L.off_otab - L.off_coef;
+  size_t iv = 0;
+  const int ntot = p.nx + p.ny + p.nz;
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < n[a]; ++i, ++iv) {
+      const double x = (i - 0.5 * (n[a] - 1)) * h[a];
+      const double V = 0.5 * w[a] * w[a] * x * x;
+      put_real(vt + iv * L.rbytes, V);
+      put<double>(buf, ot + iv * 8, V);
+      put<double>(buf, ot + (ntot + iv) * 8, x * x);
+    }
+  GP_CUDA(s, cudaMemcpyAsync(s->base + L.off_coef, buf.data(), span, cudaMemcpyHostToDevice,
+                             s->stream));
+  GP_CUDA(s, cudaStreamSynchronize(s->stream));
+  return GP_OK;
+}
+
+__global__ void k_set_double(double* p, double v) { *p = v; }
+
+int set_scale_one(gp_solver* s) {
+  k_set_double<<<1, 1, 0, s->stream>>>(s->scale, 1.0);
+  GP_CUDA(s, cudaGetLastError());
+  return GP_OK;
+}
+
+int create_impl(const gp_params* p, void* dev_buf, size_t bytes, void* stream, gp_solver** out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return GP_ERR_ARG;
+  }
+  *out = nullptr;
+  if (const char* why = check_params(p)) {
+    g_create_error = why;
+    return GP_ERR_ARG;
+  }
+  gp_solver* s = new gp_solver();
+  s->prm = *p;
+  if (const char* why = compute_layout(p, &s->L)) {
+    g_create_error = why;
+    delete s;
+    return GP_ERR_ARG;
+  }
+  s->g = nonlinearity(p);
+  s->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    delete s;
+    return GP_ERR_CUDA;
+  }
+  if (dev_buf) {
+    if (bytes < s->L.total || (reinterpret_cast<uintptr_t>(dev_buf) % kAlign) != 0) {
+      g_create_error = "caller buffer too small or not 256-byte aligned";
+      delete s;
+      return GP_ERR_NOMEM;
+    }
+    s->base = static_cast<unsigned char*>(dev_buf);
+  } else {
+    e = cudaMalloc(&s->base, s->L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g_create_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      delete s;
+      return GP_ERR_NOMEM;
+    }
+    s->owns = true;
+  }
+  const Layout& L = s->L;
+  s->field = s->base + L.off_field;
+  s->staging = reinterpret_cast<double*>(s->base + L.off_staging);
+  s->vtab = s->base + L.off_vtab;
+  s->otab = reinterpret_cast<double*>(s->base + L.off_otab);
+  s->partials = reinterpret_cast<double*>(s->base + L.off_partials);
+  unsigned char* sc = s->base + L.off_scalars;
+  s->scale = reinterpret_cast<double*>(sc);
+  s->obs = reinterpret_cast<double*>(sc + 64);
+  s->status = reinterpret_cast<int*>(sc + 256);
+  s->counters = reinterpret_cast<unsigned int*>(sc + 320);
+
+  int rc = GP_OK;
+  auto bail = [&](int code) {
+    g_create_error = s->err;
+    gp_destroy(s);
+    return code;
+  };
+  if ((e = cudaMemsetAsync(s->base + L.off_field, 0, L.field_bytes, s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(sc, 0, 512, s->stream)) != cudaSuccess) {
+    cuda_fail(s, e, "cudaMemsetAsync");
+    return bail(GP_ERR_CUDA);
+  }
+  if ((rc = upload_tables(s)) != GP_OK) return bail(rc);
+  if ((rc = set_scale_one(s)) != GP_OK) return bail(rc);
+  size_t smax = 0;
+  for (int m = 0; m < 2; ++m)
+    for (int a = 0; a < 3; ++a) smax = std::max(smax, L.geom[m][a].smem);
+  // The attribute is per kernel and process-wide: only ever raise it, so that a
+  // smaller solver created later cannot lower it under a larger one.
+  static size_t smem_set[2] = {0, 0};
+  const int pi = L.rbytes == 8 ? 0 : 1;
+  e = cudaSuccess;
+  if (smax > smem_set[pi]) {
+    e = pi == 0 ? gpk::sweep_set_smem_limits<double>(smax) : gpk::sweep_set_smem_limits<float>(smax);
+    if (e == cudaSuccess) smem_set[pi] = smax;
+  }
+  if (e != cudaSuccess) {
+    cuda_fail(s, e, "cudaFuncSetAttribute");
+    return bail(GP_ERR_CUDA);
+  }
+  if ((rc = encode_maps(s)) != GP_OK) return bail(rc);
+  fill_sweep_params(s);
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) {
+    cuda_fail(s, e, "cudaStreamSynchronize");
+    return bail(GP_ERR_CUDA);
+  }
+  *out = s;
+  return GP_OK;
+}
+
+cudaEvent_t take_event(gp_solver* s) {
+  if (!s->pool.empty()) {
+    cudaEvent_t ev = s->pool.back();
+    s->pool.pop_back();
+    return ev;
+  }
+  cudaEvent_t ev = nullptr;
+  cudaEventCreate(&ev);
+  return ev;
+}
+
+template <class R> int run_sweep(gp_solver* s, int axis) {
+  const int m = s->is_complex ? 1 : 0;
+  const SweepParams& q = s->sp[m][axis];
+  const size_t smem = s->L.geom[m][axis].smem;
+  TimedLaunch tl{nullptr, nullptr, axis};
+  if (s->timing) {
+    tl.start = take_event(s);
+    tl.stop = take_event(s);
+    GP_CUDA(s, cudaEventRecord(tl.start, s->stream));
+  }
+  cudaError_t e;
+  if (axis == 0)
+    e = gpk::launch_sweep_x<R>(q, m == 1, smem, s->stream);
+  else if (axis == 1)
+    e = gpk::launch_sweep_y<R>(s->tmap[m][1], q, m == 1, smem, s->stream);
+  else
+    e = gpk::launch_sweep_z<R>(s->tmap[m][2], q, m == 1, smem, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "sweep launch");
+  if (s->timing) {
+    GP_CUDA(s, cudaEventRecord(tl.stop, s->stream));
+    s->pending.push_back(tl);
+  }
+  return GP_OK;
+}
+
+template <class R> int steps(gp_solver* s, long nsteps) {
+  for (long t = 0; t < nsteps; ++t)
+    for (int a = 0; a < 3; ++a) {
+      const int rc = run_sweep<R>(s, a);
+      if (rc != GP_OK) return rc;
+    }
+  return GP_OK;
+}
+
+int check_status(gp_solver* s) {
+  int st = 0;
+  GP_CUDA(s, cudaMemcpyAsync(&st, s->status, sizeof st, cudaMemcpyDeviceToHost, s->stream));
+  GP_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (st == 0) return GP_OK;
+  GP_CUDA(s, cudaMemsetAsync(s->status, 0, sizeof(int), s->stream));
+  if (st & gpk::kStatusTimeout)
+    return fail(s, GP_ERR_TIMEOUT, "a kernel's bounded wait on its tile copy ran out");
+  return fail(s, GP_ERR_NONFINITE, "the norm became non-finite or zero");
+}
+
+bool is_f64(const gp_solver* s) { return s->L.rbytes == 8; }
+
+int promote_to_complex(gp_solver* s) {
+  FieldParams f = field_params(s);  // still the real layout
+  cudaError_t e = is_f64(s) ? gpk::launch_export<double>(f, s->staging, false, true, s->stream)
+                            : gpk::launch_export<float>(f, s->staging, false, true, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "export");
+  s->is_complex = true;
+  f = field_params(s);
+  e = is_f64(s) ? gpk::launch_import<double>(f, s->staging, true, s->stream)
+                : gpk::launch_import<float>(f, s->staging, true, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "import");
+  return set_scale_one(s);
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+int gp_workspace_bytes(const gp_params* p, size_t* bytes) {
+  if (!bytes) {
+    g_create_error = "bytes is NULL";
+    return GP_ERR_ARG;
+  }
+  if (const char* why = check_params(p)) {
+    g_create_error = why;
+    return GP_ERR_ARG;
+  }
+  Layout L;
+  if (const char* why = compute_layout(p, &L)) {
+    g_create_error = why;
+    return GP_ERR_ARG;
+  }
+  *bytes = L.total;
+  return GP_OK;
+}
+
+int gp_create(const gp_params* p, void* stream, gp_solver** out) {
+  return create_impl(p, nullptr, 0, stream, out);
+}
+
+int gp_create_on(const gp_params* p, void* dev_buf, size_t bytes, void* stream, gp_solver** out) {
+  if (!dev_buf) {
+    g_create_error = "dev_buf is NULL";
+    if (out) *out = nullptr;
+    return GP_ERR_ARG;
+  }
+  return create_impl(p, dev_buf, bytes, stream, out);
+}
+
+void gp_destroy(gp_solver* s) {
+  if (!s) return;
+  if (s->stream || s->base) cudaStreamSynchronize(s->stream);
+  for (auto& t : s->pending) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  for (auto ev : s->pool) cudaEventDestroy(ev);
+  if (s->owns && s->base) cudaFree(s->base);
+  delete s;
+}
+
+int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
+  if (!s) return GP_ERR_ARG;
+  if (!(wx > 0) || !(wy > 0) || !(wz > 0) || !std::isfinite(wx) || !std::isfinite(wy) ||
+      !std::isfinite(wz))
+    return fail(s, GP_ERR_ARG, "Gaussian frequencies must be finite and > 0");
+  s->is_complex = false;
+  FieldParams f = field_params(s);
+  f.out = s->scale;
+  cudaError_t e = is_f64(s) ? gpk::launch_init_gaussian<double>(f, wx, wy, wz, s->stream)
+                            : gpk::launch_init_gaussian<float>(f, wx, wy, wz, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "init_gaussian");
+  e = is_f64(s) ? gpk::launch_norm_to_scale<double>(f, s->stream)
+                : gpk::launch_norm_to_scale<float>(f, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "norm");
+  return GP_OK;
+}
+
+int gp_set_psi(gp_solver* s, const double* host, int is_complex) {
+  if (!s || !host || (is_complex != 0 && is_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  const size_t N = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
+  GP_CUDA(s, cudaMemcpyAsync(s->staging, host, N * 8 * (is_complex ? 2 : 1),
+                             cudaMemcpyHostToDevice, s->stream));
+  s->is_complex = is_complex == 1;
+  const FieldParams f = field_params(s);
+  cudaError_t e = is_f64(s) ? gpk::launch_import<double>(f, s->staging, s->is_complex, s->stream)
+                            : gpk::launch_import<float>(f, s->staging, s->is_complex, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "import");
+  return set_scale_one(s);
+}
+
+int gp_get_psi(gp_solver* s, double* host, int as_complex) {
+  if (!s || !host || (as_complex != 0 && as_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (s->is_complex && !as_complex)
+    return fail(s, GP_ERR_STATE, "the field is complex; request it with as_complex = 1");
+  const size_t N = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
+  const FieldParams f = field_params(s);
+  cudaError_t e = is_f64(s)
+                      ? gpk::launch_export<double>(f, s->staging, s->is_complex, as_complex == 1, s->stream)
+                      : gpk::launch_export<float>(f, s->staging, s->is_complex, as_complex == 1, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "export");
+  GP_CUDA(s, cudaMemcpyAsync(host, s->staging, N * 8 * (as_complex ? 2 : 1), cudaMemcpyDeviceToHost,
+                             s->stream));
+  return check_status(s);
+}
+
+int gp_step_imag(gp_solver* s, long nsteps) {
+  if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
+  if (s->is_complex) return fail(s, GP_ERR_STATE, "imaginary-time steps need a real field");
+  return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
+}
+
+int gp_step_real(gp_solver* s, long nsteps) {
+  if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
+  if (!s->is_complex) {
+    const int rc = promote_to_complex(s);
+    if (rc != GP_OK) return rc;
+  }
+  return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
+}
+
+int gp_set_g(gp_solver* s, double g) {
+  if (!s) return GP_ERR_ARG;
+  if (!std::isfinite(g)) return fail(s, GP_ERR_ARG, "g must be finite");
+  s->g = g;
+  for (int m = 0; m < 2; ++m)
+    for (int a = 0; a < 3; ++a) s->sp[m][a].g = g;
+  return GP_OK;
+}
+
+int gp_get_g(const gp_solver* s, double* g) {
+  if (!s || !g) return GP_ERR_ARG;
+  *g = s->g;
+  return GP_OK;
+}
+
+int gp_observables(gp_solver* s, gp_obs* out) {
+  if (!s || !out) return s ? fail(s, GP_ERR_ARG, "out is NULL") : GP_ERR_ARG;
+  const FieldParams f = field_params(s);
+  cudaError_t e = is_f64(s) ? gpk::launch_observables<double>(f, s->is_complex, s->stream)
+                            : gpk::launch_observables<float>(f, s->is_complex, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "observables");
+  double o[10];
+  GP_CUDA(s, cudaMemcpyAsync(o, s->obs, sizeof o, cudaMemcpyDeviceToHost, s->stream));
+  const int rc = check_status(s);
+  if (rc != GP_OK) return rc;
+  out->norm = o[0];
+  out->mu = o[1];
+  out->energy = o[2];
+  out->ekin = o[3];
+  out->epot = o[4];
+  out->eint = o[5];
+  out->rms_x = o[6];
+  out->rms_y = o[7];
+  out->rms_z = o[8];
+  out->rms_r = o[9];
+  return GP_OK;
+}
+
+int gp_density2d(gp_solver* s, int plane, double* out) {
+  if (!s || !out || plane < 0 || plane > 2) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  const gp_params& p = s->prm;
+  const FieldParams f = field_params(s);
+  cudaError_t e = is_f64(s) ? gpk::launch_density2d<double>(f, s->is_complex, plane, s->staging, s->stream)
+                            : gpk::launch_density2d<float>(f, s->is_complex, plane, s->staging, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "density2d");
+  const size_t n = plane == 0 ? (size_t)p.nx * p.ny : plane == 1 ? (size_t)p.nx * p.nz
+                                                                 : (size_t)p.ny * p.nz;
+  GP_CUDA(s, cudaMemcpyAsync(out, s->staging, n * 8, cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+int gp_density1d(gp_solver* s, int axis, double* out) {
+  if (!s || !out || axis < 0 || axis > 2) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  const gp_params& p = s->prm;
+  const FieldParams f = field_params(s);
+  const int plane = axis == 2 ? 1 : 0;  // x, y from the xy plane; z from the xz plane
+  cudaError_t e = is_f64(s) ? gpk::launch_density2d<double>(f, s->is_complex, plane, s->staging, s->stream)
+                            : gpk::launch_density2d<float>(f, s->is_complex, plane, s->staging, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "density2d");
+  double* red = s->staging + (size_t)p.nx * std::max(p.ny, p.nz);
+  if (axis == 0)
+    e = gpk::launch_cols_sum(s->staging, p.ny, p.nx, p.dy, red, s->stream);   // sum over y
+  else if (axis == 1)
+    e = gpk::launch_rows_sum(s->staging, p.ny, p.nx, p.dx, red, s->stream);   // sum over x
+  else
+    e = gpk::launch_rows_sum(s->staging, p.nz, p.nx, p.dx, red, s->stream);   // sum over x
+  if (e != cudaSuccess) return cuda_fail(s, e, "density1d");
+  const size_t n = axis == 0 ? p.nx : axis == 1 ? p.ny : p.nz;
+  GP_CUDA(s, cudaMemcpyAsync(out, red, n * 8, cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+int gp_sync(gp_solver* s) {
+  if (!s) return GP_ERR_ARG;
+  return check_status(s);
+}
+
+int gp_set_timing(gp_solver* s, int enable) {
+  if (!s) return GP_ERR_ARG;
+  s->timing = enable != 0;
+  return GP_OK;
+}
+
+int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]) {
+  if (!s || !ms || !launches) return GP_ERR_ARG;
+  GP_CUDA(s, cudaStreamSynchronize(s->stream));
+  for (int a = 0; a < 3; ++a) {
+    ms[a] = 0.0;
+    launches[a] = 0;
+  }
+  for (auto& t : s->pending) {
+    float el = 0.f;
+    GP_CUDA(s, cudaEventElapsedTime(&el, t.start, t.stop));
+    ms[t.axis] += el;
+    launches[t.axis] += 1;
+    s->pool.push_back(t.start);
+    s->pool.push_back(t.stop);
+  }
+  s->pending.clear();
+  return GP_OK;
+}
+
+int gp_get_info(const gp_solver* s, long long info[6]) {
+  if (!s || !info) return GP_ERR_ARG;
+  const int m = s->is_complex ? 1 : 0;
+  info[0] = s->L.pitch[m];
+  info[1] = m;
+  info[2] = s->L.geom[m][0].lines;
+  info[3] = s->L.geom[m][1].lines;
+  info[4] = s->L.geom[m][2].lines;
+  info[5] = (long long)s->L.total;
+  return GP_OK;
+}
+
+const char* gp_last_error(const gp_solver* s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+const char* gp_strerror(int code) {
+  switch (code) {
+    case GP_OK: return "ok";
+    case GP_ERR_ARG: return "invalid argument";
+    case GP_ERR_NOMEM: return "out of device memory or buffer too small";
+    case GP_ERR_CUDA: return "CUDA error";
+    case GP_ERR_NONFINITE: return "non-finite or zero norm";
+    case GP_ERR_TIMEOUT: return "kernel wait timed out";
+    case GP_ERR_STATE: return "invalid in the current mode";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

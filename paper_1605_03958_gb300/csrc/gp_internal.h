@@ -1,0 +1,102 @@
+// gp_internal.h -- declarations shared by the host runtime (gp_api.cu) and the
+// kernel translation units (gp_sweeps.cu, gp_reduce.cu).  Not part of the ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace gpk {
+
+// Status bits written by kernels into the solver's device status word.
+constexpr int kStatusNonFinite = 1;  // norm non-finite or zero (imaginary time)
+constexpr int kStatusTimeout = 2;    // a bounded wait on a tile copy ran out
+
+// Bounded waits on a block's own copies give up after this much wall time.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Largest grid extent per axis accepted by the ABI.
+constexpr int kMaxExtent = 2048;
+// Longest line segment one TMA box covers (hardware limit on a box dimension).
+constexpr int kMaxBox = 256;
+
+// Fixed launch shape of the reductions, so that their summation order (and hence
+// their result) does not depend on the device.
+constexpr int kReduceBlocks = 608;
+constexpr int kReduceThreads = 256;
+
+// Number of FP64 accumulators of the observables pass:
+// 0 sum|psi|^2, 1 sum V|psi|^2, 2 sum|psi|^4, 3..5 edge sums along x, y, z,
+// 6..8 sum x^2|psi|^2, y^2.., z^2..
+constexpr int kObsAcc = 9;
+
+// Arguments of one sweep launch.  Coefficient arrays hold R (real field) or the
+// complex pair of R (complex field):
+//   A_j = m_j (1 - 2a),  B_j = a m_j,  with m_j the Thomas pivots (see gp_api.cu).
+struct SweepParams {
+  void* psi;             // field base, layout [nz][ny][pitch]
+  int nx, ny, nz;
+  int pitch;             // row pitch of the field in elements
+  int n;                 // line length along the swept axis
+  int lines;             // lines per tile (one lane per line)
+  int tiles_x;           // x-tiles per (j or k) for the y / z sweeps
+  int box;               // TMA box length along the swept axis
+  int nbox;              // boxes per line
+  int words_per_elem;    // 1 real, 2 complex (TMA coordinates are in words)
+  const void* A;
+  const void* B;
+  // pointwise substep (x sweep only)
+  const void* vx;
+  const void* vy;
+  const void* vz;
+  double dt, g;
+  const double* scale;   // pending renormalisation factor, applied on load
+  // fused norm (z sweep, imaginary time only)
+  double* partials;
+  unsigned int* counter;
+  double* scale_out;
+  int* status;
+  double dV;
+  long long ntiles;
+};
+
+// Arguments of the reductions and conversion kernels.
+struct FieldParams {
+  void* psi;
+  int nx, ny, nz, pitch;
+  const double* scale;
+  double* partials;
+  unsigned int* counter;
+  double* out;           // result (observables: 10 values; norm: the scale)
+  int* status;
+  const double* tab;     // FP64 tables: V_x[nx] V_y[ny] V_z[nz] x^2[nx] y^2[ny] z^2[nz]
+  double hx, hy, hz, g;
+};
+
+// Kernel launchers (gp_sweeps.cu / gp_reduce.cu).  R = double or float storage.
+template <class R> cudaError_t launch_sweep_x(const SweepParams& p, bool complex_field,
+                                              size_t smem, cudaStream_t st);
+template <class R> cudaError_t launch_sweep_y(const CUtensorMap& map, const SweepParams& p,
+                                              bool complex_field, size_t smem, cudaStream_t st);
+template <class R> cudaError_t launch_sweep_z(const CUtensorMap& map, const SweepParams& p,
+                                              bool complex_field, size_t smem, cudaStream_t st);
+template <class R> cudaError_t sweep_set_smem_limits(size_t max_smem);
+
+template <class R> cudaError_t launch_observables(const FieldParams& p, bool complex_field,
+                                                  cudaStream_t st);
+template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaStream_t st);
+template <class R> cudaError_t launch_init_gaussian(const FieldParams& p, double wx, double wy,
+                                                    double wz, cudaStream_t st);
+template <class R> cudaError_t launch_import(const FieldParams& p, const double* src,
+                                             bool complex_field, cudaStream_t st);
+template <class R> cudaError_t launch_export(const FieldParams& p, double* dst,
+                                             bool complex_field, bool as_complex, cudaStream_t st);
+template <class R> cudaError_t launch_density2d(const FieldParams& p, bool complex_field,
+                                                int plane, double* out, cudaStream_t st);
+cudaError_t launch_rows_sum(const double* in, int rows, int cols, double w, double* out,
+                            cudaStream_t st);
+cudaError_t launch_cols_sum(const double* in, int rows, int cols, double w, double* out,
+                            cudaStream_t st);
+
+}  // namespace gpk
