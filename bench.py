@@ -1,0 +1,392 @@
+"""Benchmark: grid-point SSCN steps per second of the 3D Gross-Pitaevskii solver.
+
+Workload (paper-scale imaginary-time ground state): grid 240 x 200 x 160, h = 0.1
+(box centred on the origin), dt = 0.1 h^2, trap ratios (1, 1.41, 2), g = 100, field
+stored in FP32 (default) or FP64 with FP64 reductions, started from the g = 0 trap
+Gaussian.  One benchmark step is one full SSCN time step: pointwise substep, CN
+sweeps along x, y and z, norm and renormalisation factor.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the
+solver's stream; a 256 MiB device buffer is rewritten between timed steps so that
+every step starts with a cold L2 (the FP32 field is 31 MB, below the 135 MB L2).
+Per-sweep durations come from the library's own events on the same stream.
+`value` = (ranks x grid points x K) / max over ranks of the summed step time.
+
+Multi-GPU: every rank runs an independent replica of the solve (the solve itself
+does not shard), so scaling is weak and no collective touches the data path.
+
+`--impl reference` times the CPU oracle (plain FP64 C, OpenMP over independent
+line solves) on the same metric, each step a z-slab sample of the same grid.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY, NZ, H = 240, 200, 160, 0.1
+DT = 0.1 * H * H
+TRAP = (1.0, 1.41, 2.0)
+G = 100.0
+NPTS = NX * NY * NZ
+FLUSH_BYTES = 256 << 20
+WORKLOAD = "imag3d 240x200x160, h=0.1, dt=0.1h^2, trap (1,1.41,2), g=100, imaginary time"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--f64-steps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, nargs=3, default=None,
+                    help="override the grid (profiling of out-of-L2 cases); h and dt unchanged")
+    args = ap.parse_args()
+    if args.grid:
+        global NX, NY, NZ, NPTS, WORKLOAD
+        NX, NY, NZ = args.grid
+        NPTS = NX * NY * NZ
+        WORKLOAD = WORKLOAD.replace("240x200x160", f"{NX}x{NY}x{NZ}")
+    return args
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.06)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("gp_sweeps.cu", "gp_device.cuh", "gp_internal.h", "gp_api.cu"):
+        with open(os.path.join(ROOT, "paper_1605_03958_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+
+
+# ------------------------------------------------------------ CUDA arm
+
+def run_cuda(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_03958_gb300 as P
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    sbytes = 4 if args.prec == "f32" else 8
+    s = P.Solver(NX, NY, NZ, H, dt=DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G,
+                 prec=args.prec)
+    s.init_gaussian()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        s.step_imag(1)
+        flush.zero_()
+    s.sync()
+    torch.cuda.synchronize()
+    barrier()
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    P.gp_set_timing(s.handle, True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        for k in range(K):
+            ev0[k].record()
+            s.step_imag(1)
+            ev1[k].record()
+            flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+    kms, kn = P.gp_get_timing(s.handle)
+    P.gp_set_timing(s.handle, False)
+    s.sync()
+    step_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(K))
+    total_ms = max_over_ranks(step_ms)
+    value = world * NPTS * K / (total_ms / 1e3)
+
+    # per-sweep roofline: algorithmic bytes = one read + one write of the field
+    hbm, peak_kind = peaks()
+    names = ["sweep_x", "sweep_y", "sweep_z"]
+    kernels = {"sweep_x": f"k_sweep_x<{'float' if sbytes == 4 else 'double'},false>",
+               "sweep_y": f"k_sweep_y<{'float' if sbytes == 4 else 'double'},false>",
+               "sweep_z": f"k_sweep_z<{'float' if sbytes == 4 else 'double'},false,true>"}
+    per = {}
+    for i, n in enumerate(names):
+        avg = kms[i] / max(kn[i], 1)
+        gbs = 2 * NPTS * sbytes / (avg / 1e3) / 1e9
+        per[n] = {"avg_ms": round(avg, 5), "launches": kn[i], "achieved_gbs": round(gbs, 1),
+                  "frac": round(gbs / hbm, 3)}
+    dom = max(names, key=lambda n: per[n]["avg_ms"])
+    traffic = ncu_traffic(kernels[dom])
+    roofline = {"bound": "hbm", "kernel": kernels[dom], "achieved": per[dom]["achieved_gbs"],
+                "peak": hbm, "unit": "GB/s", "frac": per[dom]["frac"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": 2 * NPTS * sbytes,
+                "peak_source": f"{peak_kind} hbm_gbs (copy, MEASURED_PEAKS.json)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+    # end to end through the public API: H2D of the step's input field from pinned
+    # host memory, one step, D2H of the resulting field into pinned host memory
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = torch.empty(NPTS, dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty(NPTS, dtype=torch.float64, pin_memory=True)
+        P.gp.gp_get_psi_ptr(s.handle, host_in.data_ptr(), False)
+        for _ in range(3):
+            P.gp.gp_set_psi_ptr(s.handle, host_in.data_ptr(), False)
+            s.step_imag(1)
+            P.gp.gp_get_psi_ptr(s.handle, host_out.data_ptr(), False)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            P.gp.gp_set_psi_ptr(s.handle, host_in.data_ptr(), False)
+            s.step_imag(1)
+            P.gp.gp_get_psi_ptr(s.handle, host_out.data_ptr(), False)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": round(world * NPTS * args.e2e_steps / e2e_s, 1), "unit": "grid-point-steps/s",
+               "h2d_bytes_per_step": NPTS * 8, "d2h_bytes_per_step": NPTS * 8,
+               "steps": args.e2e_steps,
+               "api": "gp_set_psi(pinned FP64 host field) + gp_step_imag(1) + gp_get_psi(pinned)"}
+
+    # context: the same step back to back with L2 kept warm (no flush), one call
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    s.step_imag(K)
+    b.record()
+    torch.cuda.synchronize()
+    warm_ms = a.elapsed_time(b) / K
+
+    # the other storage precision, same protocol on fewer steps
+    other = None
+    if args.f64_steps > 0:
+        oprec = "f64" if args.prec == "f32" else "f32"
+        so = P.Solver(NX, NY, NZ, H, dt=DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G, prec=oprec)
+        so.init_gaussian()
+        for _ in range(3):
+            so.step_imag(1)
+            flush.zero_()
+        torch.cuda.synchronize()
+        P.gp_set_timing(so.handle, True)
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.f64_steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.f64_steps)]
+        for k in range(args.f64_steps):
+            e0[k].record()
+            so.step_imag(1)
+            e1[k].record()
+            flush.zero_()
+        torch.cuda.synchronize()
+        oms, okn = P.gp_get_timing(so.handle)
+        so.sync()
+        ototal = sum(e0[k].elapsed_time(e1[k]) for k in range(args.f64_steps))
+        ob = 8 if oprec == "f64" else 4
+        other = {"prec": oprec, "value": round(NPTS * args.f64_steps / (ototal / 1e3), 1),
+                 "ms_per_step": round(ototal / args.f64_steps, 5), "steps": args.f64_steps,
+                 "sweeps_avg_ms": [round(oms[i] / max(okn[i], 1), 5) for i in range(3)],
+                 "hbm_frac_per_sweep": [round(2 * NPTS * ob / (oms[i] / max(okn[i], 1) / 1e3) / 1e9 / hbm, 3)
+                                        for i in range(3)]}
+        so.close()
+
+    obs = s.observables()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    line = {
+        "metric": "grid-point SSCN steps/s", "value": round(value, 1),
+        "unit": "grid-point-steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / K, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "field": args.prec,
+                   "reductions": "f64", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB device write)",
+                   "steps_per_sample": 1},
+        "roofline": roofline, "sweeps": per,
+        "e2e": e2e, "gpu_launches": 3 * K,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "context": {"warm_l2_ms_per_step": round(warm_ms, 5),
+                    "warm_l2_value": round(NPTS / (warm_ms / 1e3), 1),
+                    "other_precision": other,
+                    "mu_after_run": obs["mu"], "norm_after_run": obs["norm"]},
+    }
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# ------------------------------------------------------- CPU oracle timings
+
+def _oracle_sample(nz_s, steps, threads):
+    import oracle
+    oracle.set_threads(threads)
+    p = oracle.Problem(NX, NY, nz_s, H, H, H, DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G)
+    psi = oracle.init_gaussian(p)
+    t0 = time.perf_counter()
+    oracle.step_imag(p, psi, steps)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline():
+    """The oracle as it stands on this host's cores, full grid, bounded to ~20 s."""
+    threads = os.cpu_count() or 1
+    t1 = _oracle_sample(NZ, 1, threads)
+    steps = max(1, min(100, int(20.0 / max(t1, 1e-3))))
+    t = _oracle_sample(NZ, steps, threads)
+    return {"value": round(NPTS * steps / t, 1), "unit": "grid-point-steps/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{steps} FP64 imaginary-time steps of the full 240x200x160 grid, "
+                      f"OpenMP over line solves on {threads} threads"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.lib()
+    threads = os.cpu_count() or 1
+    # each step: one oracle SSCN step on a 240x200xnz_s slab of the grid, nz_s sized so
+    # that the whole warm-up + timed run stays near 90 s of CPU time
+    probe = _oracle_sample(16, 1, threads) / 16.0          # seconds per z-plane-step
+    budget = 90.0 / max(args.steps + args.warmup, 1)
+    nz_s = int(max(3, min(NZ, budget / max(probe, 1e-9))))
+    if args.warmup:
+        _oracle_sample(nz_s, args.warmup, threads)
+    t = _oracle_sample(nz_s, args.steps, threads)
+    value = NX * NY * nz_s * args.steps / t
+    line = {"impl": "reference", "metric": "grid-point SSCN steps/s", "value": round(value, 1),
+            "unit": "grid-point-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "sample_grid": [NX, NY, nz_s]},
+            "cpu_baseline": {"value": round(value, 1), "unit": "grid-point-steps/s",
+                             "cores": threads, "kind": "oracle",
+                             "sample": f"each step one FP64 SSCN step of a 240x200x{nz_s} slab, "
+                                       f"OpenMP over line solves on {threads} threads"},
+            "e2e": {"value": round(value, 1), "unit": "grid-point-steps/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()
