@@ -180,8 +180,35 @@ int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]);
  *   info[5] device bytes in use.                                                 */
 int gp_get_info(const gp_solver* s, long long info[6]);
 
-/* Last error message of s, or of the calling thread's last failed gp_create /
- * gp_create_on when s is NULL.  Never NULL.                                      */
+/* Observables of a field that sits in the caller's own device memory, computed
+ * without allocating anything.  Meant for callers that cannot call cudaMalloc (which
+ * gp_create needs): cudaMalloc synchronises the whole device and so stalls the other
+ * streams of a latency-bound loop, it can fail while the free memory is held by
+ * another allocator such as PyTorch's caching allocator, and some host programs that
+ * load this library as a plugin do not allow device allocation in their callbacks.
+ *   psi        device pointer; layout psi[k][j][i] with a row pitch of `pitch`
+ *              elements (>= nx); prec GP_F64 (double) or GP_F32 (float); is_complex 1
+ *              for interleaved (re, im) values.  The field is used as it is (no
+ *              pending renormalisation).
+ *   dx..lambda, g   grid spacings, trap ratios and nonlinearity, as in gp_params.
+ *   out        device pointer to 10 doubles, written in gp_obs order with the gp_obs
+ *              definitions, once `stream` (a cudaStream_t, or NULL) reaches the work;
+ *              the call itself returns as soon as the work is queued.
+ * The reduction's scratch is a fixed 64 KiB array inside the library, held by every
+ * GPU that loads the library until the process exits and shared by all calls: calls
+ * whose work may overlap on the GPU (different streams with no ordering) race on it;
+ * issue them on one stream.  The first call on a device looks up that array's device
+ * address, which can load the library's GPU code: make this first call before any
+ * stream capture begins.  Extents beyond 1..2048 or pitch < nx return GP_ERR_ARG,
+ * with the reason in gp_last_error(NULL).  No cudaMalloc / cudaFree is called.
+ * The paper has no counterpart; this is an operational variant of gp_observables.  */
+int gp_observables_noalloc(const void* psi, int nx, int ny, int nz, long long pitch,
+                           int prec, int is_complex, double dx, double dy, double dz,
+                           double gamma, double nu, double lambda, double g, double* out,
+                           void* stream);
+
+/* Last error message of s, or, when s is NULL, of the calling thread's last failed
+ * gp_create / gp_create_on / gp_workspace_bytes / gp_observables_noalloc.  Never NULL. */
 const char* gp_last_error(const gp_solver* s);
 
 /* Static text for a GP_* code. */

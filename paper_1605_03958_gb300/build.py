@@ -1,6 +1,6 @@
 """Build the CUDA library libgp_sscn.so (sm_103a) in-tree.
 
-Three translation units compile in parallel with nvcc, then link into one shared
+The translation units compile in parallel with nvcc, then link into one shared
 library with the CUDA runtime linked statically, so the library carries no
 dependency on the runtime version PyTorch ships.  Output:
 paper_1605_03958_gb300/_build/libgp_sscn.so.
@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgp_sscn.so")
-SOURCES = ["gp_api.cu", "gp_sweeps.cu", "gp_reduce.cu"]
+SOURCES = ["gp_api.cu", "gp_sweeps.cu", "gp_reduce.cu", "gp_noalloc.cu"]
 HEADERS = ["gp_device.cuh", "gp_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

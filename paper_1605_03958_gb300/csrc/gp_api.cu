@@ -25,8 +25,13 @@ using gpk::FieldParams;
 using gpk::SweepParams;
 
 namespace {
-
 thread_local std::string g_create_error = "no error";
+}
+
+void gpk::set_thread_error(const char* msg) { g_create_error = msg; }
+
+namespace {
+
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr size_t kAlign = 256;
 constexpr size_t kFastTileBytes = 100 * 1024;   // preferred tile: >= 2 blocks per SM

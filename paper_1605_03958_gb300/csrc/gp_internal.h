@@ -99,4 +99,7 @@ cudaError_t launch_rows_sum(const double* in, int rows, int cols, double w, doub
 cudaError_t launch_cols_sum(const double* in, int rows, int cols, double w, double* out,
                             cudaStream_t st);
 
+// Message returned by gp_last_error(NULL) on this thread (gp_api.cu).
+void set_thread_error(const char* msg);
+
 }  // namespace gpk

@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_set_timing": (i, [vp, i]),
         "gp_get_timing": (i, [vp, dp, ctypes.POINTER(ll)]),
         "gp_get_info": (i, [vp, ctypes.POINTER(ll)]),
+        "gp_observables_noalloc": (i, [vp, i, i, i, ll, i, i, d, d, d, d, d, d, d, vp, vp]),
         "gp_last_error": (ctypes.c_char_p, [vp]),
         "gp_strerror": (ctypes.c_char_p, [i]),
     }
@@ -231,6 +232,17 @@ def gp_get_info(h) -> dict:
     _check(load_library().gp_get_info(h, v), h)
     keys = ("pitch", "is_complex", "lines_x", "lines_y", "lines_z", "bytes")
     return dict(zip(keys, list(v)))
+
+
+def gp_observables_noalloc(psi_ptr: int, nx: int, ny: int, nz: int, pitch: int, prec: int,
+                           is_complex: bool, dx: float, dy: float, dz: float, gamma: float,
+                           nu: float, lam: float, g: float, out_ptr: int, stream: int = 0) -> None:
+    """Observables of a field in the caller's device memory into 10 doubles of the
+    caller's device memory, without any device allocation (see include/gp.h)."""
+    rc = load_library().gp_observables_noalloc(
+        ctypes.c_void_p(psi_ptr), nx, ny, nz, pitch, prec, int(is_complex), dx, dy, dz,
+        gamma, nu, lam, g, ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
+    _check(rc)
 
 
 def gp_last_error(h=None) -> str:
