@@ -174,11 +174,16 @@ int gp_sync(gp_solver* s);
 int gp_set_timing(gp_solver* s, int enable);
 int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]);
 
-/* Layout facts of a solver, for tests and tools:
+/* Layout facts of a solver in its current mode, for tests and tools:
  *   info[0] field pitch along x in elements, info[1] 1 if the field is complex,
- *   info[2..4] lines per CTA tile of the x / y / z sweeps,
- *   info[5] device bytes in use.                                                 */
-int gp_get_info(const gp_solver* s, long long info[6]);
+ *   info[2..4] lines per shared-memory tile of the x / y / z tile kernels,
+ *   info[5] device bytes in use,
+ *   info[6] bit a set when sweep a (0 x, 1 y, 2 z) uses the FP32 kernels without
+ *           shared-memory tiles (truncated decaying coupling, see gp_sweeps.cu),
+ *   info[7] their truncation depth L (0 when none is used).
+ * GP_SWEEP_KERNELS=tile in the environment at gp_create time makes every sweep
+ * use the tile kernels.                                                          */
+int gp_get_info(const gp_solver* s, long long info[8]);
 
 /* Observables of a field that sits in the caller's own device memory, computed
  * without allocating anything.  Meant for callers that cannot call cudaMalloc (which

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -181,6 +182,13 @@ void cn_coefficients(int n, std::complex<double> a, std::vector<std::complex<dou
   }
 }
 
+// GP_SWEEP_KERNELS=tile makes every sweep use the shared-memory tile kernels
+// (diagnostics and A/B measurements); any other value or none: automatic choice.
+bool force_tile() {
+  const char* v = std::getenv("GP_SWEEP_KERNELS");
+  return v && std::strcmp(v, "tile") == 0;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -221,6 +229,10 @@ struct gp_solver {
   unsigned int* counters = nullptr;  // [0] sweeps, [1] reductions
   double* obs = nullptr;
   SweepParams sp[2][3];
+  int head[2][3] = {};               // see SweepParams::head
+  int trunc[2][3] = {};              // FP32 fast sweeps: truncation depth, 0 = use the tile kernel
+  int fast_grid[2][3] = {};          // blocks of 128 threads for the fast sweeps
+  int nsm = 0;
   CUtensorMap tmap[2][3];  // [mode][axis]; axis 0 unused (64-byte aligned type)
   // timing
   bool timing = false;
@@ -308,6 +320,7 @@ void fill_sweep_params(gp_solver* s) {
       SweepParams& q = s->sp[m][a];
       std::memset(&q, 0, sizeof q);
       q.psi = s->field;
+      q.out = s->field;
       q.nx = p.nx;
       q.ny = p.ny;
       q.nz = p.nz;
@@ -320,6 +333,7 @@ void fill_sweep_params(gp_solver* s) {
       q.words_per_elem = m + 1;
       q.A = coef + s->L.coef_off[m][a][0];
       q.B = coef + s->L.coef_off[m][a][1];
+      q.head = s->head[m][a];
       q.vx = vt;
       q.vy = vt + (size_t)p.nx * rb;
       q.vz = vt + (size_t)(p.nx + p.ny) * rb;
@@ -332,6 +346,45 @@ void fill_sweep_params(gp_solver* s) {
       q.status = s->status;
       q.dV = p.dx * p.dy * p.dz;
       q.ntiles = s->L.ntiles_z[m];
+      q.trunc = s->trunc[m][a];
+      if (q.trunc) {
+        const int tiles32 = (p.nx + 31) / 32;
+        q.tiles_x = tiles32;
+        q.seg = 0;   // x: streaming kernel (8 / 16: the windowed kernel)
+        const long long rows = (long long)p.ny * p.nz;
+        long long warps = rows;
+        if (a > 0) {
+          // split lines into segments: choose the count that best fills whole waves of
+          // resident warps, charging each segment its 2L+1 elements of warm-up;
+          // segments stay >= 4 (L+1) long
+          const long long lines = (long long)tiles32 * (a == 1 ? p.nz : p.ny);
+          const long long cap =
+              (long long)s->nsm * gpk::stream_warps_per_sm(a, m == 1, q.trunc);
+          const int nmax = std::max(1, n[a] / (4 * (q.trunc + 1)));
+          int nseg = 1;
+          double best = 0.0;
+          for (int c = 1; c <= nmax; ++c) {
+            const long long items = lines * c;
+            const long long waves = (items + cap - 1) / cap;
+            const double fill = (double)items / (double)(waves * cap);
+            const int seglen = (n[a] + c - 1) / c;
+            const double work = (double)(seglen + (c > 1 ? 2 * q.trunc + 1 : q.trunc)) / seglen;
+            const double eff = fill / work;
+            if (eff > best * 1.02) {
+              best = eff;
+              nseg = c;
+            }
+          }
+          // one FP64 norm partial per block must fit the partials area
+          while (nseg > 1 && (lines * nseg + 3) / 4 > (long long)s->L.npartials) --nseg;
+          q.nseg = nseg;
+          warps = lines * q.nseg;
+          q.psi = a == 1 ? (void*)s->field : (void*)s->staging;
+          q.out = a == 1 ? (void*)s->staging : (void*)s->field;
+        }
+        long long blocks = (warps + 3) / 4;   // x: capped at the resident grid by the launcher
+        s->fast_grid[m][a] = (int)blocks;
+      }
     }
 }
 
@@ -360,6 +413,27 @@ int upload_tables(gp_solver* s) {
                                                 : std::complex<double>(0.0, beta);
       std::vector<std::complex<double>> A, B;
       cn_coefficients(n[a], alpha, &A, &B);
+      // first index from which every coefficient, rounded to the storage precision,
+      // equals the last one: the kernels keep that value in registers
+      auto rounded = [&](std::complex<double> c) {
+        return f64 ? c : std::complex<double>((float)c.real(), (float)c.imag());
+      };
+      int head = n[a];
+      while (head > 0 && rounded(A[head - 1]) == rounded(A[n[a] - 1]) &&
+             rounded(B[head - 1]) == rounded(B[n[a] - 1]))
+        --head;
+      s->head[m][a] = head;
+      // FP32: the coupling beyond distance L, |B|^L, must stay below 2^-30
+      s->trunc[m][a] = 0;
+      if (!f64 && head <= 8 && !force_tile()) {
+        const double bmag = std::abs(rounded(B[n[a] - 1]));
+        for (int depth : {3, 5, 8})
+          if (std::pow(bmag, depth + 1) <= std::ldexp(1.0, -30)) {
+            s->trunc[m][a] = depth;
+            break;
+          }
+        // x: the streaming kernel needs head <= 32 - L (chunk geometry): always true here
+      }
       for (int ab = 0; ab < 2; ++ab) {
         const std::vector<std::complex<double>>& C = ab == 0 ? A : B;
         size_t off = L.coef_off[m][a][ab];
@@ -373,6 +447,10 @@ int upload_tables(gp_solver* s) {
         }
       }
     }
+  // the FP32 y / z kernels write out of place (y: field -> staging, z: staging ->
+  // field), so they are used together or not at all
+  for (int m = 0; m < 2; ++m)
+    if (!s->trunc[m][1] || !s->trunc[m][2]) s->trunc[m][1] = s->trunc[m][2] = 0;
   // potential tables V_a(x) = w_a^2 x^2 / 2 in storage precision, and FP64 copies + x^2
   const size_t vt = L.off_vtab - L.off_coef, ot = L.off_otab - L.off_coef;
   size_t iv = 0;
@@ -419,6 +497,8 @@ int create_impl(const gp_params* p, void* dev_buf, size_t bytes, void* stream, g
   s->g = nonlinearity(p);
   s->stream = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
   if (e != cudaSuccess) {
     g_create_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
     delete s;
@@ -514,7 +594,9 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
     GP_CUDA(s, cudaEventRecord(tl.start, s->stream));
   }
   cudaError_t e;
-  if (axis == 0)
+  if (q.trunc)
+    e = gpk::launch_sweep_fast(axis, q, m == 1, s->fast_grid[m][axis], s->stream);
+  else if (axis == 0)
     e = gpk::launch_sweep_x<R>(q, m == 1, smem, s->stream);
   else if (axis == 1)
     e = gpk::launch_sweep_y<R>(s->tmap[m][1], q, m == 1, smem, s->stream);
@@ -774,7 +856,7 @@ int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]) {
   return GP_OK;
 }
 
-int gp_get_info(const gp_solver* s, long long info[6]) {
+int gp_get_info(const gp_solver* s, long long info[8]) {
   if (!s || !info) return GP_ERR_ARG;
   const int m = s->is_complex ? 1 : 0;
   info[0] = s->L.pitch[m];
@@ -783,6 +865,8 @@ int gp_get_info(const gp_solver* s, long long info[6]) {
   info[3] = s->L.geom[m][1].lines;
   info[4] = s->L.geom[m][2].lines;
   info[5] = (long long)s->L.total;
+  info[6] = (s->trunc[m][0] ? 1 : 0) | (s->trunc[m][1] ? 2 : 0) | (s->trunc[m][2] ? 4 : 0);
+  info[7] = std::max(s->trunc[m][0], std::max(s->trunc[m][1], s->trunc[m][2]));
   return GP_OK;
 }
 

@@ -35,7 +35,8 @@ constexpr int kObsAcc = 9;
 // complex pair of R (complex field):
 //   A_j = m_j (1 - 2a),  B_j = a m_j,  with m_j the Thomas pivots (see gp_api.cu).
 struct SweepParams {
-  void* psi;             // field base, layout [nz][ny][pitch]
+  void* psi;             // field read by the sweep, layout [nz][ny][pitch]
+  void* out;             // field written (== psi except for the FP32 y / z sweeps)
   int nx, ny, nz;
   int pitch;             // row pitch of the field in elements
   int n;                 // line length along the swept axis
@@ -46,6 +47,10 @@ struct SweepParams {
   int words_per_elem;    // 1 real, 2 complex (TMA coordinates are in words)
   const void* A;
   const void* B;
+  int head;              // coefficients j >= head equal entry n-1 exactly (in storage precision)
+  int trunc;             // FP32 fast sweeps: truncation depth L of the decaying coupling
+  int seg;               // FP32 fast x sweep: elements per lane
+  int nseg;              // FP32 fast y / z sweeps: segments per line
   // pointwise substep (x sweep only)
   const void* vx;
   const void* vy;
@@ -82,6 +87,12 @@ template <class R> cudaError_t launch_sweep_y(const CUtensorMap& map, const Swee
 template <class R> cudaError_t launch_sweep_z(const CUtensorMap& map, const SweepParams& p,
                                               bool complex_field, size_t smem, cudaStream_t st);
 template <class R> cudaError_t sweep_set_smem_limits(size_t max_smem);
+// FP32 shared-memory-free sweeps (x: windowed, one warp per row; y, z: streaming,
+// one lane per line); grid in blocks of 128 threads.
+cudaError_t launch_sweep_fast(int axis, const SweepParams& p, bool complex_field, int grid,
+                              cudaStream_t st);
+// Resident warps per SM of the streaming y / z kernel (occupancy calculator).
+int stream_warps_per_sm(int axis, bool complex_field, int trunc);
 
 template <class R> cudaError_t launch_observables(const FieldParams& p, bool complex_field,
                                                   cudaStream_t st);

@@ -25,14 +25,24 @@
 //
 // Thomas recurrence with precomputed elimination coefficients for the system
 // (1+2a) u_j - a (u_{j-1} + u_{j+1}) = (1-2a) v_j + a (v_{j-1} + v_{j+1}):
-//   forward   d_j = A_j v_j + B_j (v_{j-1} + v_{j+1} + d_{j-1}),
+//   forward   d_j = B_j d_{j-1} + [A_j v_j + B_j (v_{j-1} + v_{j+1})],
 //   back      u_j = d_j + B_j u_{j+1},
 // with A_j = m_j (1 - 2a), B_j = a m_j and m_j the pivots (computed in FP64 on
-// the host).  The forward values overwrite the tile in place; the three values
-// v_{j-1}, v_j, v_{j+1} the right-hand side needs ride in registers.
+// the host).  Only the first FMA of each line is on the recurrence's dependency
+// chain; the bracket is computed off it.  The forward values overwrite the tile in
+// place; the neighbours v_{j-1}, v_j, v_{j+1} ride in registers and the next kU
+// tile values are loaded a chunk ahead, so shared-memory latency is off the chain.
+// The pivots converge geometrically; from index `head` on, the coefficients rounded
+// to the storage precision are all equal to the last one (the host checks this
+// exactly), so the bulk of a line takes them from registers and only the first
+// `head` entries come from the table.
+#include <algorithm>
+
 #include "gp_device.cuh"
 
 namespace gpk {
+
+constexpr int kU = 8;  // elements loaded ahead of the recurrence
 
 // ----------------------------------------------------------- field policies
 
@@ -47,10 +57,11 @@ template <class R> struct Field<R, false> {
   static __device__ __forceinline__ E pointwise(E v, R V, R dt, R g) {
     return v * gp_exp(-dt * fma(g * v, v, V));
   }
-  static __device__ __forceinline__ E forward(E A, E B, E prev, E next, E dprev, E cur) {
-    return fma(B, prev + next + dprev, A * cur);
+  // off-chain part of the forward step: A v_j + B (v_{j-1} + v_{j+1})
+  static __device__ __forceinline__ E rhs(E A, E B, E prev, E next, E cur) {
+    return fma(B, prev + next, A * cur);
   }
-  static __device__ __forceinline__ E back(E B, E unext, E d) { return fma(B, unext, d); }
+  static __device__ __forceinline__ E chain(E B, E x, E c) { return fma(B, x, c); }
   static __device__ __forceinline__ R abs2(E v) { return v * v; }
 };
 
@@ -66,12 +77,17 @@ template <class R> struct Field<R, true> {
     gp_sincos(th, &sn, &cs);
     return E{fma(v.x, cs, v.y * sn), fma(v.y, cs, -v.x * sn)};
   }
-  static __device__ __forceinline__ E forward(E A, E B, E prev, E next, E dprev, E cur) {
-    return cfma(B, cadd(cadd(prev, next), dprev), cmul(A, cur));
+  static __device__ __forceinline__ E rhs(E A, E B, E prev, E next, E cur) {
+    return cfma(B, cadd(prev, next), cmul(A, cur));
   }
-  static __device__ __forceinline__ E back(E B, E unext, E d) { return cfma(B, unext, d); }
+  static __device__ __forceinline__ E chain(E B, E x, E c) { return cfma(B, x, c); }
   static __device__ __forceinline__ R abs2(E v) { return fma(v.x, v.x, v.y * v.y); }
 };
+
+template <class E>
+__device__ __forceinline__ E coef(const E* T, int j, int head, E bulk) {
+  return j < head ? __ldg(T + j) : bulk;
+}
 
 // ------------------------------------------------------------------ sweep x
 
@@ -108,32 +124,65 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
     const R dt = (R)p.dt, g = (R)p.g;
     const E* A = static_cast<const E*>(p.A);
     const E* B = static_cast<const E*>(p.B);
+    const int head = p.head;
+    const E Ab = __ldg(A + nx - 1), Bb = __ldg(B + nx - 1);
     E* row = tile + (size_t)lane * P;
-    const int sig = (P & 1) ? 0 : 1;  // skew the wavefront when the pitch is even
+    // Lane l walks its row delayed by `off` steps: at step t it handles element
+    // t - off.  With an even pitch the 32 lanes then touch 32 different banks.
+    const int sig = (P & 1) ? 0 : 1;
+    const int off = sig * lane;
     const int span = nx + sig * (W - 1);
+    // element idx after the pending scale and the pointwise substep (0 outside)
+    auto load = [&](int idx) -> E {
+      if (idx < 0 || idx >= nx) return F::zero();
+      return F::pointwise(F::scaled(row[idx], s), __ldg(vx + idx) + vyz, dt, g);
+    };
 
     E prev = F::zero(), dprev = F::zero();
-    E cur = F::pointwise(F::scaled(row[0], s), __ldg(vx) + vyz, dt, g);
-    for (int t = 0; t < span; ++t) {
-      const int i = t - sig * lane;
-      if (i >= 0 && i < nx) {
-        E next = F::zero();
-        if (i + 1 < nx) next = F::pointwise(F::scaled(row[i + 1], s), __ldg(vx + i + 1) + vyz, dt, g);
-        const E d = F::forward(__ldg(A + i), __ldg(B + i), prev, next, dprev, cur);
-        row[i] = d;
-        prev = cur;
-        cur = next;
-        dprev = d;
+    E cur = load(0);
+    E nxt[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) nxt[u] = load(u + 1 - off);
+    for (int tc = 0; tc < span; tc += kU) {
+      E pre[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) pre[u] = load(tc + kU + u + 1 - off);
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = tc + u - off;
+        if (i >= 0 && i < nx) {
+          const E b = coef(B, i, head, Bb);
+          const E d = F::chain(b, dprev, F::rhs(coef(A, i, head, Ab), b, prev, nxt[u], cur));
+          row[i] = d;
+          prev = cur;
+          cur = nxt[u];
+          dprev = d;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) nxt[u] = pre[u];
     }
+    // back substitution, element nx-1-(t-off) at step t
+    auto rd = [&](int idx) -> E { return (idx >= 0 && idx < nx) ? row[idx] : F::zero(); };
     E unext = F::zero();
-    for (int t = 0; t < span; ++t) {
-      const int i = nx - 1 - (t - sig * lane);
-      if (i >= 0 && i < nx) {
-        const E u = F::back(__ldg(B + i), unext, row[i]);
-        row[i] = u;
-        unext = u;
+    E dv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) dv[u] = rd(nx - 1 + off - u);
+    for (int tc = 0; tc < span; tc += kU) {
+      E pre[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) pre[u] = rd(nx - 1 + off - tc - kU - u);
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = nx - 1 + off - tc - u;
+        if (i >= 0 && i < nx) {
+          const E v = F::chain(coef(B, i, head, Bb), unext, dv[u]);
+          row[i] = v;
+          unext = v;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) dv[u] = pre[u];
     }
   }
   fence_smem_to_async();
@@ -152,36 +201,65 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
 template <class R, bool CPLX, bool NORM>
 __device__ __forceinline__ double solve_columns(typename Field<R, CPLX>::E* tile, int W, int n,
                                                 const typename Field<R, CPLX>::E* A,
-                                                const typename Field<R, CPLX>::E* B) {
+                                                const typename Field<R, CPLX>::E* B,
+                                                int head) {
   using F = Field<R, CPLX>;
   using E = typename F::E;
   const int lane = threadIdx.x;
   double acc = 0.0;
   if (lane >= W) return acc;
   E* col = tile + lane;
+  const E Ab = __ldg(A + n - 1), Bb = __ldg(B + n - 1);
+  auto rd = [&](int j) -> E { return (j >= 0 && j < n) ? col[(size_t)j * W] : F::zero(); };
+
   E prev = F::zero(), dprev = F::zero(), cur = col[0];
-  for (int j = 0; j < n; ++j) {
-    const E next = (j + 1 < n) ? col[(size_t)(j + 1) * W] : F::zero();
-    const E d = F::forward(__ldg(A + j), __ldg(B + j), prev, next, dprev, cur);
-    col[(size_t)j * W] = d;
-    prev = cur;
-    cur = next;
-    dprev = d;
+  E nxt[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) nxt[u] = rd(u + 1);
+  for (int j0 = 0; j0 < n; j0 += kU) {
+    E pre[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) pre[u] = rd(j0 + kU + u + 1);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 + u;
+      if (j < n) {
+        const E b = coef(B, j, head, Bb);
+        const E d = F::chain(b, dprev, F::rhs(coef(A, j, head, Ab), b, prev, nxt[u], cur));
+        col[(size_t)j * W] = d;
+        prev = cur;
+        cur = nxt[u];
+        dprev = d;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) nxt[u] = pre[u];
   }
+
   E unext = F::zero();
   R part = R(0);
-  int cnt = 0;
-  for (int j = n - 1; j >= 0; --j) {
-    const E u = F::back(__ldg(B + j), unext, col[(size_t)j * W]);
-    col[(size_t)j * W] = u;
-    unext = u;
-    if (NORM) {
-      part += F::abs2(u);
-      if (++cnt == 16) {
-        acc += (double)part;
-        part = R(0);
-        cnt = 0;
+  E dv[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) dv[u] = rd(n - 1 - u);
+  for (int j0 = n - 1; j0 >= 0; j0 -= kU) {
+    E pre[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) pre[u] = rd(j0 - kU - u);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 - u;
+      if (j >= 0) {
+        const E v = F::chain(coef(B, j, head, Bb), unext, dv[u]);
+        col[(size_t)j * W] = v;
+        unext = v;
+        if (NORM) part += F::abs2(v);
       }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) dv[u] = pre[u];
+    if (NORM && ((n - 1 - j0) / kU) % 2 == 1) {  // fold into FP64 every 16 elements
+      acc += (double)part;
+      part = R(0);
     }
   }
   if (NORM) acc += (double)part;
@@ -214,7 +292,7 @@ __global__ void __launch_bounds__(32) k_sweep_y(const __grid_constant__ CUtensor
   __syncwarp();
   if (!wait_tile(bar, p.status)) return;
   solve_columns<R, CPLX, false>(tile, W, p.n, static_cast<const E*>(p.A),
-                                static_cast<const E*>(p.B));
+                                static_cast<const E*>(p.B), p.head);
   fence_smem_to_async();
   __syncwarp();
   if (lane == 0) {
@@ -251,7 +329,7 @@ __global__ void __launch_bounds__(32) k_sweep_z(const __grid_constant__ CUtensor
   double acc = 0.0;
   if (wait_tile(bar, p.status)) {
     acc = solve_columns<R, CPLX, NORM>(tile, W, p.n, static_cast<const E*>(p.A),
-                                       static_cast<const E*>(p.B));
+                                       static_cast<const E*>(p.B), p.head);
     fence_smem_to_async();
     __syncwarp();
     if (lane == 0) {
@@ -293,6 +371,457 @@ __global__ void __launch_bounds__(32) k_sweep_z(const __grid_constant__ CUtensor
   }
 }
 
+// ============================================================================
+// Shared-memory-free FP32 sweeps (real and complex fields).
+//
+// In the bulk of a line every rounded coefficient equals (A, B) (see `head`), and
+// |B| < 1, so the coupling between elements decays like |B|^distance.  The host
+// picks a truncation depth L with |B|^(L+1) <= 2^-30 (below an FP32 ulp); both
+// kernels below cut the coupling there and are otherwise the same recurrence:
+//  * back substitution u_e = d_e + B u_{e+1} in the bulk equals the series
+//    sum_{m>=0} B^m d_{e+m}; cut after m = L it becomes a Horner sum over the
+//    last L+1 forward values, so a line streams in one direction: u_e is
+//    emitted L elements behind the forward recurrence.  At the line end the
+//    series ends on its own (d = 0 past the last element: the exact boundary);
+//    the first `head` elements, whose coefficients differ, are finished exactly
+//    by the recurrence from u_head.
+//  * a segment of a line can be solved by a lane that starts the forward
+//    recurrence L+1 elements before the segment (from d = 0) and the back
+//    recurrence L elements after it (from u = 0).
+// ============================================================================
+
+#ifndef GP_STREAM_U
+#define GP_STREAM_U 16
+#endif
+#ifndef GP_STREAM_MINB
+#define GP_STREAM_MINB 6
+#endif
+constexpr int kStreamU = GP_STREAM_U;  // chunk length of the streaming kernel (load lead)
+constexpr int kHeadMax = 8;     // largest `head` the streaming kernel handles
+
+// Fixed-order block reduction of one FP64 value per warp into partials[block];
+// the last block to finish sums the partials (all its threads, loads issued ahead,
+// a fixed-order tree) and writes the renormalisation factor.  Every thread of the
+// block must call it.
+__device__ __forceinline__ void norm_block_finish(double acc, const SweepParams& p) {
+  __shared__ double wpart[32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) wpart[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += wpart[w];
+    p.partials[blockIdx.x] = v;
+    __threadfence();
+    last = (atomicAdd(p.counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // thread t sums partials t, t + blockDim, ... (8 loads in flight), then a tree
+  const unsigned int nb = gridDim.x, T = blockDim.x;
+  double s = 0.0, c = 0.0;
+  for (unsigned int t0 = threadIdx.x; t0 < nb; t0 += 8 * T) {
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const unsigned int t = t0 + q * T;
+      x[q] = t < nb ? __ldcg(p.partials + t) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double u = s + x[q];
+      c += (fabs(s) >= fabs(x[q])) ? (s - u) + x[q] : (x[q] - u) + s;
+      s = u;
+    }
+  }
+  s += c;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) wpart[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < nw; ++w) tot += wpart[w];
+    const double norm = tot * p.dV;
+    if (!(norm > 0.0) || !isfinite(norm)) atomicOr(p.status, kStatusNonFinite);
+    *p.scale_out = 1.0 / sqrt(norm);
+    *p.counter = 0u;
+  }
+}
+
+// y (AXIS 1) or z (AXIS 2) sweep: one lane per line, lanes on consecutive x.  A
+// line is split into p.nseg segments handled by different warps; a warp streams
+// its segment [s0, s1) with direct coalesced loads, starting the forward
+// recurrence L+1 elements early (from d = 0).  The back substitution runs per
+// chunk of U elements, L behind the forward: the top element of the chunk is
+// seeded by the truncated series sum_{m<=L} B^m d_{e+m}, the rest follow from the
+// exact recurrence u_e = d_e + B_e u_{e+1} (table coefficients for e < head).
+// The result goes to p.out (not in place: neighbouring segments read each
+// other's inputs).
+template <class R, bool CPLX, int AXIS, bool NORM, int L>
+__global__ void __launch_bounds__(128, CPLX ? 4 : GP_STREAM_MINB) k_sweep_stream(const SweepParams p) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  constexpr int U = kStreamU;
+  static_assert(L < U && kHeadMax <= U - L, "chunk geometry");
+  const int lane = threadIdx.x & 31;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int tiles_x = p.tiles_x, nseg = p.nseg;
+  const int nother = AXIS == 1 ? p.nz : p.ny;
+  const bool live = wid < (long long)tiles_x * nother * nseg;
+  double acc = 0.0;
+  if (live) {
+    const int w = (int)wid;
+    const int sg = w % nseg;
+    const int lw = w / nseg;
+    const int tx = lw % tiles_x, o = lw / tiles_x;
+    const int i = tx * 32 + lane;
+    const bool act = i < p.nx;
+    const size_t P = (size_t)p.pitch;
+    // lanes past nx mirror column 0 (valid addresses); they store nothing and add
+    // nothing to the norm
+    const size_t base = (AXIS == 1 ? (size_t)o * p.ny * P : (size_t)o * P) + (act ? i : 0);
+    const E* lin = static_cast<const E*>(p.psi) + base;
+    E* lout = static_cast<E*>(p.out) + base;
+    const size_t st = AXIS == 1 ? P : P * p.ny;
+    const int n = p.n, head = p.head;
+    const int seglen = (n + nseg - 1) / nseg;
+    const int s0 = sg * seglen, s1 = min(n, s0 + seglen);
+    const int js = sg == 0 ? 0 : max(0, s0 - L - 1);   // forward start (d = 0 before it)
+    const E* A = static_cast<const E*>(p.A);
+    const E* B = static_cast<const E*>(p.B);
+    const E Ab = __ldg(A + n - 1), Bb = __ldg(B + n - 1);
+
+    E prev = js > 0 ? lin[(size_t)(js - 1) * st] : F::zero();
+    E cur = lin[(size_t)js * st];
+    E dprev = F::zero();
+    E nv[U], tail[L];
+    const E* lp = lin + (size_t)(js + 1) * st;   // next element to load
+    int jl = js + 1;                              // its index
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      nv[u] = jl < n ? *lp : F::zero();
+      lp += st;
+      ++jl;
+    }
+#pragma unroll
+    for (int q = 0; q < L; ++q) tail[q] = F::zero();
+    R part = R(0);
+    for (int j0 = js; j0 < s1 + L; j0 += U) {
+      E dd[U];
+      // forward; each consumed slot of nv is refilled at once with the element U
+      // further on, so U loads stay in flight with one register array
+      const bool full_load = jl + U <= n;
+      if (j0 >= head && j0 + U <= n) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const E nx = nv[u];
+          nv[u] = (full_load || jl + u < n) ? *lp : F::zero();
+          lp += st;
+          const E d = F::chain(Bb, dprev, F::rhs(Ab, Bb, prev, nx, cur));
+          prev = cur;
+          cur = nx;
+          dprev = d;
+          dd[u] = d;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const E nx = nv[u];
+          nv[u] = (full_load || jl + u < n) ? *lp : F::zero();
+          lp += st;
+          const int j = j0 + u;
+          if (j < n) {
+            const E b = coef(B, j, head, Bb);
+            const E d = F::chain(b, dprev, F::rhs(coef(A, j, head, Ab), b, prev, nx, cur));
+            prev = cur;
+            cur = nx;
+            dprev = d;
+            dd[u] = d;
+          } else {
+            dd[u] = F::zero();
+          }
+        }
+      }
+      jl += U;
+      // back: elements e = j0 - L + u, u = U-1 .. 0; seed at the top
+      E un;
+      {
+        un = dd[U - 1];
+#pragma unroll
+        for (int m = L - 1; m >= 0; --m) un = F::chain(Bb, un, dd[U - 1 - L + m]);
+      }
+      const int ebase = j0 - L;
+      const bool all_out = ebase >= s0 && ebase + U <= s1 && ebase >= head;
+      E* op = lout + (ptrdiff_t)(ebase + U - 1) * (ptrdiff_t)st;
+      if (all_out) {
+#pragma unroll
+        for (int u = U - 1; u >= 0; --u) {
+          if (u < U - 1) {  // d_{ebase+u}: dd[u-L] for u >= L, else tail[u]
+            const E dv = u >= L ? dd[u >= L ? u - L : 0] : tail[u < L ? u : 0];
+            un = F::chain(Bb, un, dv);
+          }
+          if (act) *op = un;
+          op -= st;
+          if (NORM && act) part += F::abs2(un);
+        }
+      } else {
+#pragma unroll
+        for (int u = U - 1; u >= 0; --u) {
+          const int e = ebase + u;
+          if (u < U - 1) {
+            const E dv = u >= L ? dd[u >= L ? u - L : 0] : tail[u < L ? u : 0];
+            const E b = (e >= 0 && e < head) ? __ldg(B + e) : Bb;
+            un = F::chain(b, un, dv);
+          }
+          if (e >= s0 && e < s1 && act) {
+            *op = un;
+            if (NORM) part += F::abs2(un);
+          }
+          op -= st;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < L; ++q) tail[q] = dd[U - L + q];
+      if (NORM) {
+        acc += (double)part;
+        part = R(0);
+      }
+    }
+  }
+  if (NORM) norm_block_finish(acc, p);
+}
+
+// x sweep with the fused pending scale and pointwise substep, streaming form: one
+// warp per 32 consecutive rows (lane l owns row r0 + l) in a 32-thread block.  The
+// rows advance together in chunks of kXC elements: a chunk of the 32 rows is
+// copied with coalesced 4/8-byte cp.async (zero fill past nx) into a padded
+// shared-memory tile (stride kXC+1: lane l reading its row touches bank l+u), three
+// chunks in flight.  Forward recurrence and the seeded block-backward are those of
+// k_sweep_stream; outputs go through a padded tile and leave as coalesced stores.
+// Each warp owns whole rows, so the sweep is in place.
+constexpr int kXC = 32;            // chunk length along x
+constexpr int kXS = kXC + 1;       // padded row stride of a chunk tile
+
+template <class R, bool CPLX, int L>
+__global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  constexpr int C = kXC;
+  static_assert(L < C && kHeadMax <= C - L, "chunk geometry");
+  extern __shared__ __align__(16) unsigned char smem[];
+  E* ib = reinterpret_cast<E*>(smem);          // 3 input tiles [32][kXS]
+  E* ob = ib + 3 * 32 * kXS;                    // output tile [32][kXS]
+  const int lane = threadIdx.x;
+  const long long nrows = (long long)p.ny * p.nz;
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int rows = (int)min(32LL, nrows - r0);
+  const int nx = p.nx, head = p.head;
+  const size_t P = (size_t)p.pitch;
+  E* field = static_cast<E*>(p.psi) + (size_t)r0 * P;
+  const E* A = static_cast<const E*>(p.A);
+  const E* B = static_cast<const E*>(p.B);
+  const E Ab = __ldg(A + nx - 1), Bb = __ldg(B + nx - 1);
+  const R* vx = static_cast<const R*>(p.vx);
+  const R s = (R)(*p.scale);
+  const R dt = (R)p.dt, g = (R)p.g;
+  const long long myrow = r0 + min(lane, rows - 1);
+  const int jrow = (int)(myrow % p.ny), krow = (int)(myrow / p.ny);
+  const R vyz = __ldg(static_cast<const R*>(p.vy) + jrow) + __ldg(static_cast<const R*>(p.vz) + krow);
+  const int nchunk = (nx + C - 1) / C;
+
+  // chunk c of all 32 rows -> tile c % 3 (always commits a group, maybe empty)
+  auto issue = [&](int c) {
+    if (c < nchunk) {
+      E* t = ib + (c % 3) * 32 * kXS;
+      const int j = c * C + lane;
+      const bool okj = j < nx;
+      for (int q = 0; q < 32; ++q) {
+        const bool ok = okj && q < rows;
+        const E* src = field + (ok ? (size_t)q * P + j : 0);   // in bounds even when zero-filling
+        cp_async_zfill<sizeof(E)>(t + q * kXS + lane, src, ok);
+      }
+    }
+    cp_async_commit();
+  };
+  // element u of chunk c of this lane's row, after scale and pointwise substep
+  auto val = [&](int c, int u) -> E {
+    const int j = c * C + u;
+    if (j >= nx) return F::zero();
+    const E raw = ib[(c % 3) * 32 * kXS + lane * kXS + u];
+    return F::pointwise(F::scaled(raw, s), __ldg(vx + j) + vyz, dt, g);
+  };
+
+  issue(0);
+  issue(1);
+  E prev = F::zero(), dprev = F::zero(), cur = F::zero();
+  E tail[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) tail[q] = F::zero();
+  for (int c = 0; c * C < nx + L; ++c) {
+    const int j0 = c * C;
+    issue(c + 2);
+    cp_async_wait<1>();   // chunks c and c+1 have landed
+    __syncwarp();
+    if (c == 0) cur = val(0, 0);
+    E dd[C];
+    if (j0 >= head && j0 + C <= nx) {
+#pragma unroll
+      for (int u = 0; u < C; ++u) {
+        const E nx_ = (u + 1 < C) ? val(c, u + 1) : val(c + 1, 0);
+        const E d = F::chain(Bb, dprev, F::rhs(Ab, Bb, prev, nx_, cur));
+        prev = cur;
+        cur = nx_;
+        dprev = d;
+        dd[u] = d;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < C; ++u) {
+        const int j = j0 + u;
+        if (j < nx) {
+          const E nx_ = (u + 1 < C) ? val(c, u + 1) : val(c + 1, 0);
+          const E b = coef(B, j, head, Bb);
+          const E d = F::chain(b, dprev, F::rhs(coef(A, j, head, Ab), b, prev, nx_, cur));
+          prev = cur;
+          cur = nx_;
+          dprev = d;
+          dd[u] = d;
+        } else {
+          dd[u] = F::zero();
+        }
+      }
+    }
+    // back: e = j0 - L + u, seeded at the top of the chunk by the truncated series
+    E un = dd[C - 1];
+#pragma unroll
+    for (int m = L - 1; m >= 0; --m) un = F::chain(Bb, un, dd[C - 1 - L + m]);
+    const int ebase = j0 - L;
+    const bool bulk = ebase >= head;
+#pragma unroll
+    for (int u = C - 1; u >= 0; --u) {
+      if (u < C - 1) {
+        const E dv = u >= L ? dd[u >= L ? u - L : 0] : tail[u < L ? u : 0];
+        const int e = ebase + u;
+        const E b = (!bulk && e >= 0 && e < head) ? __ldg(B + e) : Bb;
+        un = F::chain(b, un, dv);
+      }
+      ob[lane * kXS + u] = un;
+    }
+#pragma unroll
+    for (int q = 0; q < L; ++q) tail[q] = dd[C - L + q];
+    __syncwarp();
+    // coalesced store of the finished elements e = ebase + lane of every row
+    {
+      const int e = ebase + lane;
+      if (e >= 0 && e < nx)
+        for (int q = 0; q < rows; ++q) field[(size_t)q * P + e] = ob[q * kXS + lane];
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+}
+
+// x sweep with the fused pending scale and pointwise substep: one warp per row,
+// lane l owns elements [l S, l S + S); halos of L+1 values come from the
+// neighbouring lanes by shuffles.  Rows are assigned to warps round-robin, and
+// the next row's segment is loaded while the current one is solved.
+template <class R, bool CPLX, int L, int S>
+__global__ void __launch_bounds__(128) k_sweep_x_window(const SweepParams p) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  static_assert(S >= L + 1, "halos come from one neighbour");
+  const int lane = threadIdx.x & 31;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nrows = (long long)p.ny * p.nz;
+  const int nx = p.nx, head = p.head;
+  const size_t P = (size_t)p.pitch;
+  const int s0 = lane * S;
+  const E* A = static_cast<const E*>(p.A);
+  const E* B = static_cast<const E*>(p.B);
+  const E Ab = __ldg(A + nx - 1), Bb = __ldg(B + nx - 1);
+  const R* vx = static_cast<const R*>(p.vx);
+  const R* vy = static_cast<const R*>(p.vy);
+  const R* vz = static_cast<const R*>(p.vz);
+  const R s = (R)(*p.scale);
+  const R dt = (R)p.dt, g = (R)p.g;
+  R vxs[S];
+#pragma unroll
+  for (int q = 0; q < S; ++q) vxs[q] = (s0 + q < nx) ? __ldg(vx + s0 + q) : R(0);
+
+  auto load_row = [&](long long r, E (&seg)[S]) {
+    const E* row = static_cast<const E*>(p.psi) + (size_t)r * P;
+#pragma unroll
+    for (int q = 0; q < S; ++q) seg[q] = (s0 + q < nx) ? row[s0 + q] : F::zero();
+  };
+  // two rows in flight ahead of the one being solved
+  E nxt[S], nxt2[S];
+  if (wid < nrows) load_row(wid, nxt);
+  if (wid + nwarps < nrows) load_row(wid + nwarps, nxt2);
+  for (long long r = wid; r < nrows; r += nwarps) {
+    E own[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      own[q] = nxt[q];
+      nxt[q] = nxt2[q];
+    }
+    if (r + 2 * nwarps < nrows) load_row(r + 2 * nwarps, nxt2);
+    const int j = (int)(r % p.ny), k = (int)(r / p.ny);
+    const R vyz = __ldg(vy + j) + __ldg(vz + k);
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      own[q] = (s0 + q < nx) ? F::pointwise(F::scaled(own[q], s), vxs[q] + vyz, dt, g) : F::zero();
+    // window w = 0 .. S+2L+1 holds v at j = s0 - L - 1 + w
+    E win[S + 2 * L + 2];
+#pragma unroll
+    for (int q = 0; q <= L; ++q) {
+      E left = own[S - L - 1 + q], right = own[q];
+      if constexpr (CPLX) {
+        left.x = __shfl_up_sync(0xffffffffu, left.x, 1);
+        left.y = __shfl_up_sync(0xffffffffu, left.y, 1);
+        right.x = __shfl_down_sync(0xffffffffu, right.x, 1);
+        right.y = __shfl_down_sync(0xffffffffu, right.y, 1);
+      } else {
+        left = __shfl_up_sync(0xffffffffu, left, 1);
+        right = __shfl_down_sync(0xffffffffu, right, 1);
+      }
+      win[q] = lane == 0 ? F::zero() : left;
+      win[S + L + 1 + q] = lane == 31 ? F::zero() : right;
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q) win[L + 1 + q] = own[q];
+    // forward over j = s0 - L .. s0 + S + L - 1 (window positions 1 .. S+2L)
+    E dd[S + L];
+    E dprev = F::zero();
+#pragma unroll
+    for (int w = 1; w <= S + 2 * L; ++w) {
+      const int jj = s0 - L - 1 + w;
+      const bool in = jj >= 0 && jj < nx;
+      const E b = in ? coef(B, jj, head, Bb) : Bb;
+      const E a = in ? coef(A, jj, head, Ab) : Ab;
+      const E d = in ? F::chain(b, dprev, F::rhs(a, b, win[w - 1], win[w + 1], win[w])) : F::zero();
+      dprev = d;
+      if (w >= L + 1) dd[w - L - 1] = d;
+    }
+    // back from j = s0 + S + L - 1 down to s0 (u = 0 above the window / past nx-1)
+    E unext = F::zero();
+#pragma unroll
+    for (int q = S + L - 1; q >= 0; --q) {
+      const int jj = s0 + q;
+      const E u = jj < nx ? F::chain(coef(B, jj, head, Bb), unext, dd[q]) : F::zero();
+      unext = u;
+      if (q < S) own[q] = u;
+    }
+    E* row = static_cast<E*>(p.psi) + (size_t)r * P;
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      if (s0 + q < nx) row[s0 + q] = own[q];
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 
 template <class R>
@@ -327,6 +856,97 @@ cudaError_t launch_sweep_z(const CUtensorMap& map, const SweepParams& p, bool co
   else
     k_sweep_z<R, false, true><<<grid, 32, smem, st>>>(map, p);
   return cudaGetLastError();
+}
+
+// FP32 shared-memory-free sweeps; `trunc` is the truncation depth L (3, 5 or 8),
+// `seg` the x-sweep segment per lane (8 or 16).
+// Persistent grid of a row kernel: as many 128-thread blocks as can be resident
+// (registers decide), capped by the work; computed once per kernel.
+template <class K>
+static int resident_grid(K kernel, int want) {
+  static int per_sm = 0, nsm = 0;
+  if (!per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  return std::max(1, std::min(want, per_sm * nsm));
+}
+
+template <int L>
+static cudaError_t launch_fast_L(int axis, const SweepParams& p, bool cplx, int grid,
+                                 cudaStream_t st) {
+  if (axis == 0 && p.seg == 0) {  // streaming x kernel (1-warp blocks)
+    const size_t smem = (size_t)4 * 32 * kXS * (cplx ? 8 : 4);
+    const unsigned int blocks = (unsigned int)(((long long)p.ny * p.nz + 31) / 32);
+    if (cplx) k_sweep_x_stream<float, true, L><<<blocks, 32, smem, st>>>(p);
+    else k_sweep_x_stream<float, false, L><<<blocks, 32, smem, st>>>(p);
+    return cudaGetLastError();
+  }
+  if (axis == 0) {
+    if (p.seg == 8) {
+      if constexpr (L + 1 <= 8) {
+        if (cplx) {
+          auto k = k_sweep_x_window<float, true, L, 8>;
+          k<<<resident_grid(k, grid), 128, 0, st>>>(p);
+        } else {
+          auto k = k_sweep_x_window<float, false, L, 8>;
+          k<<<resident_grid(k, grid), 128, 0, st>>>(p);
+        }
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    } else {
+      if (cplx) {
+        auto k = k_sweep_x_window<float, true, L, 16>;
+        k<<<resident_grid(k, grid), 128, 0, st>>>(p);
+      } else {
+        auto k = k_sweep_x_window<float, false, L, 16>;
+        k<<<resident_grid(k, grid), 128, 0, st>>>(p);
+      }
+    }
+  } else if (axis == 1) {
+    if (cplx) k_sweep_stream<float, true, 1, false, L><<<grid, 128, 0, st>>>(p);
+    else k_sweep_stream<float, false, 1, false, L><<<grid, 128, 0, st>>>(p);
+  } else {
+    if (cplx) k_sweep_stream<float, true, 2, false, L><<<grid, 128, 0, st>>>(p);
+    else k_sweep_stream<float, false, 2, true, L><<<grid, 128, 0, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+template <int L>
+static int stream_warps_per_sm_L(int axis, bool cplx) {
+  int b = 0;
+  if (axis == 1) {
+    if (cplx) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_stream<float, true, 1, false, L>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_stream<float, false, 1, false, L>, 128, 0);
+  } else {
+    if (cplx) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_stream<float, true, 2, false, L>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_stream<float, false, 2, true, L>, 128, 0);
+  }
+  return 4 * std::max(b, 1);
+}
+
+int stream_warps_per_sm(int axis, bool complex_field, int trunc) {
+  switch (trunc) {
+    case 3: return stream_warps_per_sm_L<3>(axis, complex_field);
+    case 5: return stream_warps_per_sm_L<5>(axis, complex_field);
+    case 8: return stream_warps_per_sm_L<8>(axis, complex_field);
+    default: return 4;
+  }
+}
+
+cudaError_t launch_sweep_fast(int axis, const SweepParams& p, bool complex_field, int grid,
+                              cudaStream_t st) {
+  switch (p.trunc) {
+    case 3: return launch_fast_L<3>(axis, p, complex_field, grid, st);
+    case 5: return launch_fast_L<5>(axis, p, complex_field, grid, st);
+    case 8: return launch_fast_L<8>(axis, p, complex_field, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class R> cudaError_t sweep_set_smem_limits(size_t max_smem) {

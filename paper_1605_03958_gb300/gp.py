@@ -18,7 +18,7 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libgp_sscn.so")
+LIB_PATH = os.environ.get("GP_SSCN_LIB") or os.path.join(_HERE, "_build", "libgp_sscn.so")
 
 GP_OK = 0
 GP_ERR_ARG = -1
@@ -228,9 +228,10 @@ def gp_get_timing(h):
 
 
 def gp_get_info(h) -> dict:
-    v = (ctypes.c_longlong * 6)()
+    v = (ctypes.c_longlong * 8)()
     _check(load_library().gp_get_info(h, v), h)
-    keys = ("pitch", "is_complex", "lines_x", "lines_y", "lines_z", "bytes")
+    keys = ("pitch", "is_complex", "lines_x", "lines_y", "lines_z", "bytes", "fast_mask",
+            "trunc")
     return dict(zip(keys, list(v)))
 
 

@@ -303,3 +303,47 @@ def test_timing_counts_launches(P, orc):
     assert n == [7, 7, 7]
     assert all(m > 0 for m in ms)
     P.gp_set_timing(s.handle, False)
+
+
+# ------------------------------------- FP32 kernels without shared-memory tiles
+
+FAST_SHAPES = [(64, 48, 32), (37, 29, 23), (240, 20, 16), (300, 40, 30), (17, 33, 19), (3, 70, 41)]
+
+
+@pytest.mark.parametrize("shape", FAST_SHAPES)
+@pytest.mark.parametrize("mode", ["imag", "real"])
+def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mode, monkeypatch):
+    """The FP32 sweeps that cut the decaying coupling at depth L (|B|^(L+1) <= 2^-30)
+    agree with the exact FP32 tile kernels to FP32 rounding, and both with the FP64
+    oracle."""
+    p = problem(orc, *shape, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=50.0, hy=0.18, hz=0.22)
+    steps = 20
+    if mode == "imag":
+        psi0 = orc.init_gaussian(p)
+        ref = orc.step_imag(p, psi0, steps)
+    else:
+        psi0 = orc.step_imag(p, orc.init_gaussian(p), 10).astype(complex)
+        ref = orc.step_real(p, psi0, steps)
+    outs = {}
+    for kind in ("auto", "tile"):
+        if kind == "tile":
+            monkeypatch.setenv("GP_SWEEP_KERNELS", "tile")
+        else:
+            monkeypatch.delenv("GP_SWEEP_KERNELS", raising=False)
+        s = solver(P, p, prec="f32")
+        s.set_psi(psi0)
+        if mode == "imag":
+            s.step_imag(steps)
+            outs[kind] = (s.get_psi(), s.info())
+        else:
+            s.step_real(steps)
+            outs[kind] = (s.get_psi(as_complex=True), s.info())
+        s.close()
+    monkeypatch.delenv("GP_SWEEP_KERNELS", raising=False)
+    assert outs["tile"][1]["fast_mask"] == 0
+    if shape[0] >= 16:
+        assert outs["auto"][1]["fast_mask"] == 7, outs["auto"][1]
+    scale = np.max(np.abs(ref))
+    for kind in outs:
+        assert np.max(np.abs(outs[kind][0] - ref)) <= 3e-6 * scale, kind
+    assert np.max(np.abs(outs["auto"][0] - outs["tile"][0])) <= 3e-6 * scale
