@@ -200,7 +200,6 @@ def run_cuda(args):
     K = args.steps
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    P.gp_set_timing(s.handle, True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         barrier()
@@ -211,12 +210,23 @@ def run_cuda(args):
             flush()
         torch.cuda.synchronize()
         barrier()
-    kms, kn = P.gp_get_timing(s.handle)
-    P.gp_set_timing(s.handle, False)
     s.sync()
     step_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(K))
     total_ms = max_over_ranks(step_ms)
     value = world * NPTS * K / (total_ms / 1e3)
+
+    # second timed region: the same steps with every sweep bracketed by the library's
+    # CUDA events on the solver stream (these events keep consecutive sweeps from
+    # overlapping, so the step timing above is taken without them)
+    K2 = min(K, 500)
+    P.gp_set_timing(s.handle, True)
+    torch.cuda.synchronize()
+    for k in range(K2):
+        s.step_imag(1)
+        flush()
+    kms, kn = P.gp_get_timing(s.handle)
+    P.gp_set_timing(s.handle, False)
+    s.sync()
 
     # per-sweep roofline: algorithmic bytes = one read + one write of the field
     hbm, peak_kind = peaks()

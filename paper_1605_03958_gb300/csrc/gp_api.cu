@@ -350,7 +350,6 @@ void fill_sweep_params(gp_solver* s) {
       if (q.trunc) {
         const int tiles32 = (p.nx + 31) / 32;
         q.tiles_x = tiles32;
-        q.seg = 0;   // x: streaming kernel (8 / 16: the windowed kernel)
         const long long rows = (long long)p.ny * p.nz;
         long long warps = rows;
         if (a > 0) {

@@ -49,7 +49,6 @@ struct SweepParams {
   const void* B;
   int head;              // coefficients j >= head equal entry n-1 exactly (in storage precision)
   int trunc;             // FP32 fast sweeps: truncation depth L of the decaying coupling
-  int seg;               // FP32 fast x sweep: elements per lane
   int nseg;              // FP32 fast y / z sweeps: segments per line
   // pointwise substep (x sweep only)
   const void* vx;
@@ -87,8 +86,8 @@ template <class R> cudaError_t launch_sweep_y(const CUtensorMap& map, const Swee
 template <class R> cudaError_t launch_sweep_z(const CUtensorMap& map, const SweepParams& p,
                                               bool complex_field, size_t smem, cudaStream_t st);
 template <class R> cudaError_t sweep_set_smem_limits(size_t max_smem);
-// FP32 shared-memory-free sweeps (x: windowed, one warp per row; y, z: streaming,
-// one lane per line); grid in blocks of 128 threads.
+// FP32 shared-memory-free sweeps (x: streaming, one lane per row, 32 rows per warp;
+// y, z: streaming, one lane per line); y / z grid in blocks of 128 threads.
 cudaError_t launch_sweep_fast(int axis, const SweepParams& p, bool complex_field, int grid,
                               cudaStream_t st);
 // Resident warps per SM of the streaming y / z kernel (occupancy calculator).

@@ -38,6 +38,8 @@
 // `head` entries come from the table.
 #include <algorithm>
 
+#include <utility>
+
 #include "gp_device.cuh"
 
 namespace gpk {
@@ -93,6 +95,7 @@ __device__ __forceinline__ E coef(const E* T, int j, int head, E bulk) {
 
 template <class R, bool CPLX>
 __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
+  pdl_begin();
   using F = Field<R, CPLX>;
   using E = typename F::E;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -271,6 +274,7 @@ __device__ __forceinline__ double solve_columns(typename Field<R, CPLX>::E* tile
 template <class R, bool CPLX>
 __global__ void __launch_bounds__(32) k_sweep_y(const __grid_constant__ CUtensorMap map,
                                                 const SweepParams p) {
+  pdl_begin();
   using E = typename Field<R, CPLX>::E;
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x;
@@ -307,6 +311,7 @@ __global__ void __launch_bounds__(32) k_sweep_y(const __grid_constant__ CUtensor
 template <class R, bool CPLX, bool NORM>
 __global__ void __launch_bounds__(32) k_sweep_z(const __grid_constant__ CUtensorMap map,
                                                 const SweepParams p) {
+  pdl_begin();
   using E = typename Field<R, CPLX>::E;
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x;
@@ -462,6 +467,7 @@ __device__ __forceinline__ void norm_block_finish(double acc, const SweepParams&
 // other's inputs).
 template <class R, bool CPLX, int AXIS, bool NORM, int L>
 __global__ void __launch_bounds__(128, CPLX ? 4 : GP_STREAM_MINB) k_sweep_stream(const SweepParams p) {
+  pdl_begin();
   using F = Field<R, CPLX>;
   using E = typename F::E;
   constexpr int U = kStreamU;
@@ -607,11 +613,12 @@ constexpr int kXS = kXC + 1;       // padded row stride of a chunk tile
 
 template <class R, bool CPLX, int L>
 __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
+  pdl_begin();
   using F = Field<R, CPLX>;
   using E = typename F::E;
   constexpr int C = kXC;
   static_assert(L < C && kHeadMax <= C - L, "chunk geometry");
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   E* ib = reinterpret_cast<E*>(smem);          // 3 input tiles [32][kXS]
   E* ob = ib + 3 * 32 * kXS;                    // output tile [32][kXS]
   const int lane = threadIdx.x;
@@ -724,104 +731,6 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
   cp_async_wait<0>();
 }
 
-// x sweep with the fused pending scale and pointwise substep: one warp per row,
-// lane l owns elements [l S, l S + S); halos of L+1 values come from the
-// neighbouring lanes by shuffles.  Rows are assigned to warps round-robin, and
-// the next row's segment is loaded while the current one is solved.
-template <class R, bool CPLX, int L, int S>
-__global__ void __launch_bounds__(128) k_sweep_x_window(const SweepParams p) {
-  using F = Field<R, CPLX>;
-  using E = typename F::E;
-  static_assert(S >= L + 1, "halos come from one neighbour");
-  const int lane = threadIdx.x & 31;
-  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nrows = (long long)p.ny * p.nz;
-  const int nx = p.nx, head = p.head;
-  const size_t P = (size_t)p.pitch;
-  const int s0 = lane * S;
-  const E* A = static_cast<const E*>(p.A);
-  const E* B = static_cast<const E*>(p.B);
-  const E Ab = __ldg(A + nx - 1), Bb = __ldg(B + nx - 1);
-  const R* vx = static_cast<const R*>(p.vx);
-  const R* vy = static_cast<const R*>(p.vy);
-  const R* vz = static_cast<const R*>(p.vz);
-  const R s = (R)(*p.scale);
-  const R dt = (R)p.dt, g = (R)p.g;
-  R vxs[S];
-#pragma unroll
-  for (int q = 0; q < S; ++q) vxs[q] = (s0 + q < nx) ? __ldg(vx + s0 + q) : R(0);
-
-  auto load_row = [&](long long r, E (&seg)[S]) {
-    const E* row = static_cast<const E*>(p.psi) + (size_t)r * P;
-#pragma unroll
-    for (int q = 0; q < S; ++q) seg[q] = (s0 + q < nx) ? row[s0 + q] : F::zero();
-  };
-  // two rows in flight ahead of the one being solved
-  E nxt[S], nxt2[S];
-  if (wid < nrows) load_row(wid, nxt);
-  if (wid + nwarps < nrows) load_row(wid + nwarps, nxt2);
-  for (long long r = wid; r < nrows; r += nwarps) {
-    E own[S];
-#pragma unroll
-    for (int q = 0; q < S; ++q) {
-      own[q] = nxt[q];
-      nxt[q] = nxt2[q];
-    }
-    if (r + 2 * nwarps < nrows) load_row(r + 2 * nwarps, nxt2);
-    const int j = (int)(r % p.ny), k = (int)(r / p.ny);
-    const R vyz = __ldg(vy + j) + __ldg(vz + k);
-#pragma unroll
-    for (int q = 0; q < S; ++q)
-      own[q] = (s0 + q < nx) ? F::pointwise(F::scaled(own[q], s), vxs[q] + vyz, dt, g) : F::zero();
-    // window w = 0 .. S+2L+1 holds v at j = s0 - L - 1 + w
-    E win[S + 2 * L + 2];
-#pragma unroll
-    for (int q = 0; q <= L; ++q) {
-      E left = own[S - L - 1 + q], right = own[q];
-      if constexpr (CPLX) {
-        left.x = __shfl_up_sync(0xffffffffu, left.x, 1);
-        left.y = __shfl_up_sync(0xffffffffu, left.y, 1);
-        right.x = __shfl_down_sync(0xffffffffu, right.x, 1);
-        right.y = __shfl_down_sync(0xffffffffu, right.y, 1);
-      } else {
-        left = __shfl_up_sync(0xffffffffu, left, 1);
-        right = __shfl_down_sync(0xffffffffu, right, 1);
-      }
-      win[q] = lane == 0 ? F::zero() : left;
-      win[S + L + 1 + q] = lane == 31 ? F::zero() : right;
-    }
-#pragma unroll
-    for (int q = 0; q < S; ++q) win[L + 1 + q] = own[q];
-    // forward over j = s0 - L .. s0 + S + L - 1 (window positions 1 .. S+2L)
-    E dd[S + L];
-    E dprev = F::zero();
-#pragma unroll
-    for (int w = 1; w <= S + 2 * L; ++w) {
-      const int jj = s0 - L - 1 + w;
-      const bool in = jj >= 0 && jj < nx;
-      const E b = in ? coef(B, jj, head, Bb) : Bb;
-      const E a = in ? coef(A, jj, head, Ab) : Ab;
-      const E d = in ? F::chain(b, dprev, F::rhs(a, b, win[w - 1], win[w + 1], win[w])) : F::zero();
-      dprev = d;
-      if (w >= L + 1) dd[w - L - 1] = d;
-    }
-    // back from j = s0 + S + L - 1 down to s0 (u = 0 above the window / past nx-1)
-    E unext = F::zero();
-#pragma unroll
-    for (int q = S + L - 1; q >= 0; --q) {
-      const int jj = s0 + q;
-      const E u = jj < nx ? F::chain(coef(B, jj, head, Bb), unext, dd[q]) : F::zero();
-      unext = u;
-      if (q < S) own[q] = u;
-    }
-    E* row = static_cast<E*>(p.psi) + (size_t)r * P;
-#pragma unroll
-    for (int q = 0; q < S; ++q)
-      if (s0 + q < nx) row[s0 + q] = own[q];
-  }
-}
-
 // ---------------------------------------------------------------- launchers
 
 template <class R>
@@ -829,92 +738,61 @@ cudaError_t launch_sweep_x(const SweepParams& p, bool complex_field, size_t smem
                            cudaStream_t st) {
   const long long nrows = (long long)p.ny * p.nz;
   const dim3 grid((unsigned int)((nrows + p.lines - 1) / p.lines));
-  if (complex_field)
-    k_sweep_x<R, true><<<grid, 32, smem, st>>>(p);
-  else
-    k_sweep_x<R, false><<<grid, 32, smem, st>>>(p);
-  return cudaGetLastError();
+  return complex_field ? launch_pdl(k_sweep_x<R, true>, grid, 32, smem, st, p)
+                       : launch_pdl(k_sweep_x<R, false>, grid, 32, smem, st, p);
 }
 
 template <class R>
 cudaError_t launch_sweep_y(const CUtensorMap& map, const SweepParams& p, bool complex_field,
                            size_t smem, cudaStream_t st) {
   const dim3 grid((unsigned int)p.tiles_x, (unsigned int)p.nz);
-  if (complex_field)
-    k_sweep_y<R, true><<<grid, 32, smem, st>>>(map, p);
-  else
-    k_sweep_y<R, false><<<grid, 32, smem, st>>>(map, p);
-  return cudaGetLastError();
+  return complex_field ? launch_pdl(k_sweep_y<R, true>, grid, 32, smem, st, map, p)
+                       : launch_pdl(k_sweep_y<R, false>, grid, 32, smem, st, map, p);
 }
 
 template <class R>
 cudaError_t launch_sweep_z(const CUtensorMap& map, const SweepParams& p, bool complex_field,
                            size_t smem, cudaStream_t st) {
   const dim3 grid((unsigned int)p.tiles_x, (unsigned int)p.ny);
-  if (complex_field)
-    k_sweep_z<R, true, false><<<grid, 32, smem, st>>>(map, p);
-  else
-    k_sweep_z<R, false, true><<<grid, 32, smem, st>>>(map, p);
-  return cudaGetLastError();
+  return complex_field ? launch_pdl(k_sweep_z<R, true, false>, grid, 32, smem, st, map, p)
+                       : launch_pdl(k_sweep_z<R, false, true>, grid, 32, smem, st, map, p);
 }
 
 // FP32 shared-memory-free sweeps; `trunc` is the truncation depth L (3, 5 or 8),
 // `seg` the x-sweep segment per lane (8 or 16).
-// Persistent grid of a row kernel: as many 128-thread blocks as can be resident
-// (registers decide), capped by the work; computed once per kernel.
-template <class K>
-static int resident_grid(K kernel, int want) {
-  static int per_sm = 0, nsm = 0;
-  if (!per_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
-    if (per_sm < 1) per_sm = 1;
-  }
-  return std::max(1, std::min(want, per_sm * nsm));
+// Launch with programmatic dependent launch allowed: the kernel's blocks may be
+// scheduled while the previous kernel of the stream drains; every sweep kernel waits
+// (griddepcontrol.wait) for that kernel's completion before touching memory.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <int L>
 static cudaError_t launch_fast_L(int axis, const SweepParams& p, bool cplx, int grid,
                                  cudaStream_t st) {
-  if (axis == 0 && p.seg == 0) {  // streaming x kernel (1-warp blocks)
+  if (axis == 0) {  // streaming x kernel (1-warp blocks)
     const size_t smem = (size_t)4 * 32 * kXS * (cplx ? 8 : 4);
     const unsigned int blocks = (unsigned int)(((long long)p.ny * p.nz + 31) / 32);
-    if (cplx) k_sweep_x_stream<float, true, L><<<blocks, 32, smem, st>>>(p);
-    else k_sweep_x_stream<float, false, L><<<blocks, 32, smem, st>>>(p);
-    return cudaGetLastError();
+    return cplx ? launch_pdl(k_sweep_x_stream<float, true, L>, blocks, 32, smem, st, p)
+                : launch_pdl(k_sweep_x_stream<float, false, L>, blocks, 32, smem, st, p);
   }
-  if (axis == 0) {
-    if (p.seg == 8) {
-      if constexpr (L + 1 <= 8) {
-        if (cplx) {
-          auto k = k_sweep_x_window<float, true, L, 8>;
-          k<<<resident_grid(k, grid), 128, 0, st>>>(p);
-        } else {
-          auto k = k_sweep_x_window<float, false, L, 8>;
-          k<<<resident_grid(k, grid), 128, 0, st>>>(p);
-        }
-      } else {
-        return cudaErrorInvalidValue;
-      }
-    } else {
-      if (cplx) {
-        auto k = k_sweep_x_window<float, true, L, 16>;
-        k<<<resident_grid(k, grid), 128, 0, st>>>(p);
-      } else {
-        auto k = k_sweep_x_window<float, false, L, 16>;
-        k<<<resident_grid(k, grid), 128, 0, st>>>(p);
-      }
-    }
-  } else if (axis == 1) {
-    if (cplx) k_sweep_stream<float, true, 1, false, L><<<grid, 128, 0, st>>>(p);
-    else k_sweep_stream<float, false, 1, false, L><<<grid, 128, 0, st>>>(p);
-  } else {
-    if (cplx) k_sweep_stream<float, true, 2, false, L><<<grid, 128, 0, st>>>(p);
-    else k_sweep_stream<float, false, 2, true, L><<<grid, 128, 0, st>>>(p);
-  }
-  return cudaGetLastError();
+  if (axis == 1)
+    return cplx ? launch_pdl(k_sweep_stream<float, true, 1, false, L>, grid, 128, 0, st, p)
+                : launch_pdl(k_sweep_stream<float, false, 1, false, L>, grid, 128, 0, st, p);
+  return cplx ? launch_pdl(k_sweep_stream<float, true, 2, false, L>, grid, 128, 0, st, p)
+              : launch_pdl(k_sweep_stream<float, false, 2, true, L>, grid, 128, 0, st, p);
 }
 
 template <int L>

@@ -310,13 +310,16 @@ def test_timing_counts_launches(P, orc):
 FAST_SHAPES = [(64, 48, 32), (37, 29, 23), (240, 20, 16), (300, 40, 30), (17, 33, 19), (3, 70, 41)]
 
 
+@pytest.mark.parametrize("g", [50.0, 3000.0])
 @pytest.mark.parametrize("shape", FAST_SHAPES)
 @pytest.mark.parametrize("mode", ["imag", "real"])
-def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mode, monkeypatch):
+def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mode, g, monkeypatch):
     """The FP32 sweeps that cut the decaying coupling at depth L (|B|^(L+1) <= 2^-30)
     agree with the exact FP32 tile kernels to FP32 rounding, and both with the FP64
-    oracle."""
-    p = problem(orc, *shape, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=50.0, hy=0.18, hz=0.22)
+    oracle.  g = 50 keeps the nonlinear phase per step near the 1/16 switch of the
+    small-argument polynomials (both branches run); g = 3000 takes the library
+    exp / sincos."""
+    p = problem(orc, *shape, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=g, hy=0.18, hz=0.22)
     steps = 20
     if mode == "imag":
         psi0 = orc.init_gaussian(p)
@@ -343,7 +346,9 @@ def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mod
     assert outs["tile"][1]["fast_mask"] == 0
     if shape[0] >= 16:
         assert outs["auto"][1]["fast_mask"] == 7, outs["auto"][1]
-    scale = np.max(np.abs(ref))
+    # FP32 rounding, amplified by the nonlinear phase (dt g |psi|^2 ~ 0.25 per step at
+    # g = 3000) over 20 steps: measured up to 3.1e-6 of max|psi| at g = 3000
+    tol = (3e-6 if g < 1000 else 1e-5) * np.max(np.abs(ref))
     for kind in outs:
-        assert np.max(np.abs(outs[kind][0] - ref)) <= 3e-6 * scale, kind
-    assert np.max(np.abs(outs["auto"][0] - outs["tile"][0])) <= 3e-6 * scale
+        assert np.max(np.abs(outs[kind][0] - ref)) <= tol, kind
+    assert np.max(np.abs(outs["auto"][0] - outs["tile"][0])) <= tol
