@@ -149,6 +149,21 @@ def ncu_traffic(kernel):
     return None if k is None else k.get("dram_bytes_per_launch_full_size")
 
 
+def replica_throughput(local_ms, units_per_rank, group=None, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    `units_per_rank` units in `local_ms`; the job took the slowest rank's time.
+    Returns (units / s over all ranks, max ms over ranks)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    ms = float(local_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 # ------------------------------------------------------------ CUDA arm
 
 def run_cuda(args):
@@ -169,12 +184,7 @@ def run_cuda(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_throughput(x, 1, device="cuda")[1]
 
     sbytes = 4 if args.prec == "f32" else 8
     s = P.Solver(NX, NY, NZ, H, dt=DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G,
@@ -212,8 +222,7 @@ def run_cuda(args):
         barrier()
     s.sync()
     step_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(K))
-    total_ms = max_over_ranks(step_ms)
-    value = world * NPTS * K / (total_ms / 1e3)
+    value, total_ms = replica_throughput(step_ms, NPTS * K, device="cuda")
 
     # second timed region: the same steps with every sweep bracketed by the library's
     # CUDA events on the solver stream (these events keep consecutive sweeps from
