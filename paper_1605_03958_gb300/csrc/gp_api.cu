@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -37,6 +38,10 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr size_t kAlign = 256;
 constexpr size_t kFastTileBytes = 100 * 1024;   // preferred tile: >= 2 blocks per SM
 constexpr size_t kMaxTileBytes = 226 * 1024;    // opt-in shared memory per block, minus slack
+constexpr int kBandHalfMax = 8;                 // band half-widths 3, 5 or 8
+constexpr int kBandMinNx = 8;                   // one reflection covers every window
+constexpr size_t kBandStageBytes = 16 * 1024;   // target bytes of one group of the x band kernel
+constexpr int kBandStages = 3;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -55,6 +60,7 @@ struct Layout {
   size_t off_field = 0, off_staging = 0, off_coef = 0, off_vtab = 0, off_otab = 0;
   size_t off_partials = 0, off_scalars = 0, total = 0;
   size_t coef_off[2][3][2] = {};   // [mode][axis][A/B] byte offset from off_coef
+  size_t vyz_off = 0;              // FP32: V_y[j] + V_z[k] per row, from off_coef
   size_t npartials = 0;
   SweepGeom geom[2][3];
   long long ntiles_z[2] = {0, 0};
@@ -151,6 +157,10 @@ const char* compute_layout(const gp_params* p, Layout* L) {
         L->coef_off[m][a][ab] = c;
         c = align_up(c + (size_t)n[a] * L->rbytes * (m + 1), kAlign);
       }
+  if (L->rbytes == 4) {
+    L->vyz_off = c;
+    c = align_up(c + rows * 4, kAlign);
+  }
   off = align_up(off + c, kAlign);
   L->off_vtab = off;
   off = align_up(off + (size_t)(p->nx + p->ny + p->nz) * L->rbytes, kAlign);
@@ -182,11 +192,53 @@ void cn_coefficients(int n, std::complex<double> a, std::vector<std::complex<dou
   }
 }
 
-// GP_SWEEP_KERNELS=tile makes every sweep use the shared-memory tile kernels
-// (diagnostics and A/B measurements); any other value or none: automatic choice.
+// GP_SWEEP_KERNELS=tile makes every sweep use the shared-memory tile kernels;
+// GP_SWEEP_KERNELS=stream keeps the FP32 x sweep on the streaming recurrence kernel
+// instead of the banded one (diagnostics and A/B measurements); any other value or
+// none: automatic choice.
 bool force_tile() {
   const char* v = std::getenv("GP_SWEEP_KERNELS");
   return v && std::strcmp(v, "tile") == 0;
+}
+bool force_stream() {
+  const char* v = std::getenv("GP_SWEEP_KERNELS");
+  return v && std::strcmp(v, "stream") == 0;
+}
+
+// Row of the free-line CN operator T_inf = (I + aK)^{-1} (I - aK) (K the second
+// difference on the infinite line): the middle row of the zero-ghost operator of a
+// line of 2 M + 1 points, M = 64, whose ghosts are so far away (|rho|^64) that their
+// influence is far below FP64 rounding for every usable a.  T is symmetric, so that
+// row is the Thomas solve (FP64) for the right-hand side (I - aK) e_M.  Returns the
+// smallest half-width W in {3, 5, 8} for which the entries beyond distance W sum, in
+// modulus, to at most 2^-28 (below FP32 rounding of a result), with
+// w[k] = T_inf[M][M + k - W], k = 0 .. 2W; 0 when no such W exists.
+int cn_free_row(std::complex<double> a, std::vector<std::complex<double>>* w) {
+  using C = std::complex<double>;
+  constexpr int M = 64, n = 2 * M + 1;
+  const C b = 1.0 + 2.0 * a;
+  std::vector<C> m(n), cp(n), d(n), u(n);
+  for (int j = 0; j < n; ++j) {
+    m[j] = 1.0 / (j == 0 ? b : b + a * cp[j - 1]);
+    cp[j] = -a * m[j];
+  }
+  C dp = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const C r = i == M ? 1.0 - 2.0 * a : (i == M - 1 || i == M + 1) ? a : C(0.0);
+    dp = (r + a * dp) * m[i];
+    d[i] = dp;
+  }
+  C next = 0.0;
+  for (int i = n - 1; i >= 0; --i) next = u[i] = d[i] - cp[i] * next;
+  for (int W : {3, 5, kBandHalfMax}) {
+    double tail = 0.0;
+    for (int i = 0; i < n; ++i)
+      if (std::abs(i - M) > W) tail += std::sqrt(std::norm(u[i]));
+    if (!(tail <= std::ldexp(1.0, -28))) continue;
+    w->assign(u.begin() + (M - W), u.begin() + (M + W + 1));
+    return W;
+  }
+  return 0;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -231,7 +283,9 @@ struct gp_solver {
   SweepParams sp[2][3];
   int head[2][3] = {};               // see SweepParams::head
   int trunc[2][3] = {};              // FP32 fast sweeps: truncation depth, 0 = use the tile kernel
-  int fast_grid[2][3] = {};          // blocks of 128 threads for the fast sweeps
+  int fast_grid[2][3] = {};          // blocks of the fast sweeps (x band: persistent grid)
+  int band_w[2] = {};                // FP32 banded x sweep half-width per mode, 0 = not used
+  float band_wt[2][2 * 17] = {};     // its weights per mode (complex: pairs)
   int nsm = 0;
   CUtensorMap tmap[2][3];  // [mode][axis]; axis 0 unused (64-byte aligned type)
   // timing
@@ -384,6 +438,31 @@ void fill_sweep_params(gp_solver* s) {
         long long blocks = (warps + 3) / 4;   // x: capped at the resident grid by the launcher
         s->fast_grid[m][a] = (int)blocks;
       }
+      if (a == 0 && s->band_w[m]) {
+        const int ept = m == 0 ? 4 : 2;
+        const int tpr = (p.nx + ept - 1) / ept;
+        q.vyz = coef + s->L.vyz_off;
+        std::memcpy(q.band_wt, s->band_wt[m], sizeof q.band_wt);
+        q.band_w = s->band_w[m];
+        q.band_tpr = tpr;
+        q.band_threads = tpr <= 256 ? 256 : (tpr + 31) / 32 * 32;
+        q.band_rp = q.band_threads / tpr;
+        const size_t slot_bytes = ((size_t)s->L.pitch[m] + 16) * rb * (m + 1);
+        const int passes = std::max<int>(1, (int)(kBandStageBytes / (slot_bytes * q.band_rp)));
+        q.band_rows = q.band_rp * passes;
+        q.band_stages = kBandStages;
+        const size_t smem = gpk::x_band_smem(q, m == 1);
+        int bps = 0;
+        const long long groups = ((long long)p.ny * p.nz + q.band_rows - 1) / q.band_rows;
+        if (gpk::x_band_prepare(q.band_w, m == 1, q.band_threads, smem, &bps) == cudaSuccess &&
+            bps > 0) {
+          s->fast_grid[m][0] = (int)std::min<long long>(groups, (long long)s->nsm * bps);
+        } else {
+          cudaGetLastError();
+          s->band_w[m] = 0;
+          q.band_w = 0;
+        }
+      }
     }
 }
 
@@ -446,6 +525,29 @@ int upload_tables(gp_solver* s) {
         }
       }
     }
+  // FP32 x sweep as a banded operator on the odd extension of each row, when a
+  // half-width <= 8 is exact to FP32 rounding and a row fits one block
+  for (int m = 0; m < 2; ++m) {
+    s->band_w[m] = 0;
+    const int ept = m == 0 ? 4 : 2;
+    if (f64 || force_tile() || force_stream() || p.nx < kBandMinNx ||
+        (p.nx + ept - 1) / ept > gpk::kBandMaxThreads)
+      continue;
+    const double beta = p.dt / (4.0 * h[0] * h[0]);
+    std::vector<std::complex<double>> w;
+    const int W = cn_free_row(m == 0 ? std::complex<double>(beta, 0.0)
+                                     : std::complex<double>(0.0, beta), &w);
+    if (!W) continue;
+    s->band_w[m] = W;
+    for (int k = 0; k <= 2 * W; ++k) {
+      if (m == 0) {
+        s->band_wt[m][k] = (float)w[k].real();
+      } else {
+        s->band_wt[m][2 * k] = (float)w[k].real();
+        s->band_wt[m][2 * k + 1] = (float)w[k].imag();
+      }
+    }
+  }
   // the FP32 y / z kernels write out of place (y: field -> staging, z: staging ->
   // field), so they are used together or not at all
   for (int m = 0; m < 2; ++m)
@@ -462,6 +564,17 @@ int upload_tables(gp_solver* s) {
       put<double>(buf, ot + iv * 8, V);
       put<double>(buf, ot + (ntot + iv) * 8, x * x);
     }
+  // FP32: the trap's y + z part per row, summed in FP32 from the FP32 tables exactly as
+  // the kernels that read V_y and V_z separately do
+  if (!f64)
+    for (int k = 0; k < p.nz; ++k)
+      for (int j = 0; j < p.ny; ++j) {
+        float vy, vz;
+        std::memcpy(&vy, buf.data() + vt + (size_t)(p.nx + j) * 4, 4);
+        std::memcpy(&vz, buf.data() + vt + (size_t)(p.nx + p.ny + k) * 4, 4);
+        const float sum = vy + vz;
+        put<float>(buf, L.vyz_off + ((size_t)k * p.ny + j) * 4, sum);
+      }
   GP_CUDA(s, cudaMemcpyAsync(s->base + L.off_coef, buf.data(), span, cudaMemcpyHostToDevice,
                              s->stream));
   GP_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -593,7 +706,9 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
     GP_CUDA(s, cudaEventRecord(tl.start, s->stream));
   }
   cudaError_t e;
-  if (q.trunc)
+  if (axis == 0 && q.band_w)
+    e = gpk::launch_sweep_x_band(q, m == 1, s->fast_grid[m][0], s->stream);
+  else if (q.trunc)
     e = gpk::launch_sweep_fast(axis, q, m == 1, s->fast_grid[m][axis], s->stream);
   else if (axis == 0)
     e = gpk::launch_sweep_x<R>(q, m == 1, smem, s->stream);
@@ -864,7 +979,8 @@ int gp_get_info(const gp_solver* s, long long info[8]) {
   info[3] = s->L.geom[m][1].lines;
   info[4] = s->L.geom[m][2].lines;
   info[5] = (long long)s->L.total;
-  info[6] = (s->trunc[m][0] ? 1 : 0) | (s->trunc[m][1] ? 2 : 0) | (s->trunc[m][2] ? 4 : 0);
+  info[6] = (s->trunc[m][0] ? 1 : 0) | (s->trunc[m][1] ? 2 : 0) | (s->trunc[m][2] ? 4 : 0) |
+            (s->band_w[m] ? 8 | (s->band_w[m] << 4) : 0);
   info[7] = std::max(s->trunc[m][0], std::max(s->trunc[m][1], s->trunc[m][2]));
   return GP_OK;
 }

@@ -64,6 +64,8 @@ template <class R> struct Field<R, false> {
     return fma(B, prev + next, A * cur);
   }
   static __device__ __forceinline__ E chain(E B, E x, E c) { return fma(B, x, c); }
+  static __device__ __forceinline__ E mul(E a, E b) { return a * b; }
+  static __device__ __forceinline__ E add(E a, E b) { return a + b; }
   static __device__ __forceinline__ R abs2(E v) { return v * v; }
 };
 
@@ -83,6 +85,8 @@ template <class R> struct Field<R, true> {
     return cfma(B, cadd(prev, next), cmul(A, cur));
   }
   static __device__ __forceinline__ E chain(E B, E x, E c) { return cfma(B, x, c); }
+  static __device__ __forceinline__ E mul(E a, E b) { return cmul(a, b); }
+  static __device__ __forceinline__ E add(E a, E b) { return cadd(a, b); }
   static __device__ __forceinline__ R abs2(E v) { return fma(v.x, v.x, v.y * v.y); }
 };
 
@@ -731,6 +735,181 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
   cp_async_wait<0>();
 }
 
+// ------------------------------------------------------- x sweep, banded operator
+
+// The CN solve of a line is linear, u = T v with T = (I + aK)^{-1} (I - aK) and K the
+// second difference with zero ghosts at -1 and n.  Reflection principle: extend v to
+// the whole line as the odd function about both ghosts (v~_{-1-m} = -v~_{-1+m},
+// v~_{n+m} = -v~_{n-m}); the free-line CN operator T_inf maps it to a function with
+// the same symmetry, hence zero at the ghosts, which therefore solves the zero-ghost
+// system: u_i = sum_k w_k v~_{i+k} with w the (symmetric) row of T_inf.  Its entries
+// decay like rho^|k| (rho the root of rho + 1/rho = (1+2a)/a inside the unit circle),
+// so in FP32 the sum stops at |k| <= W: the host takes w from an FP64 Thomas solve on
+// a long line and picks the smallest W in {3, 5, 8} whose neglected entries sum to at
+// most 2^-28.  Every output is then the same (2W+1)-tap dot product (weights in the
+// kernel parameters), with no recurrence and no per-index coefficients: all the
+// elements of a row are computed at once.
+//
+// A block is persistent over groups of band_rows consecutive rows.  Each row of a
+// group arrives by one bulk copy into a shared-memory slot with kBandPad elements of
+// room on both sides; band_stages groups are in flight.  Thread t serves the EPT
+// elements (one 16-byte vector) from x0 = EPT (t mod tpr) of rows t / tpr,
+// t / tpr + rp, ... of the group.  Per group: the pending scale and the pointwise
+// substep in shared memory, the threads at the ends of a row also writing the odd
+// images into the pads (zero at the ghosts); a block barrier; the dot products from
+// 16-byte shared loads; stores straight to the field (in place: a block owns its
+// rows).  Needs nx >= kBandPad so that one reflection covers every window.
+constexpr int kBandPad = 8;   // room for the odd images on each side of a row slot
+
+template <class R, bool CPLX, int W>
+__global__ void __launch_bounds__(kBandMaxThreads) k_sweep_x_band(const __grid_constant__ SweepParams p) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  constexpr int EPT = 16 / (int)sizeof(E);   // elements per 16-byte vector
+  constexpr int H = (W + EPT - 1) / EPT;     // halo vectors on each side of a window
+  constexpr int NV = 2 * H + 1;              // vectors in a window
+  static_assert(H * EPT <= kBandPad, "window inside the slot");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  E* slots = reinterpret_cast<E*>(smem + 128);
+  const int nx = p.nx, pitch = p.pitch;
+  const int slot = pitch + 2 * kBandPad;
+  const int R_ = p.band_rows, S = p.band_stages, tpr = p.band_tpr, rp = p.band_rp;
+  const int t = threadIdx.x;
+  const int rr = t / tpr;
+  const int x0 = (t - rr * tpr) * EPT;
+  const bool worker = rr < rp;
+  // threads whose elements have odd images in the pads, or run past nx
+  const bool edge = x0 <= kBandPad - 2 || x0 + EPT - 1 > nx - kBandPad;
+  const long long nrows = (long long)p.ny * p.nz;
+  const long long ngroups = (nrows + R_ - 1) / R_;
+  E* field = static_cast<E*>(p.psi);
+  const E* wt = reinterpret_cast<const E*>(p.band_wt);   // w_{k-W}, k = 0 .. 2W
+
+  if (t == 0)
+    for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
+  // the ghost positions -1 and pitch (= nx when nx == pitch) stay zero
+  for (int q = t; q < S * R_; q += blockDim.x) {
+    E* sl = slots + (size_t)q * slot + kBandPad;
+    sl[-1] = F::zero();
+    sl[pitch] = F::zero();
+  }
+  R vxr[EPT];
+  {
+    const R* vx = static_cast<const R*>(p.vx);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) vxr[e] = (worker && x0 + e < nx) ? __ldg(vx + x0 + e) : R(0);
+  }
+  __syncthreads();
+  pdl_begin();
+  const R s = (R)(*p.scale);
+  const R dt = (R)p.dt, g = (R)p.g;
+  const R* vyz = static_cast<const R*>(p.vyz);
+  const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
+
+  // group grp -> stage st: one bulk copy per row
+  auto issue = [&](long long grp, int st) {
+    const long long r0 = grp * R_;
+    const int rows = (int)min((long long)R_, nrows - r0);
+    mbar_arrive_expect_tx(&full[st], (uint32_t)rows * rowbytes);
+    for (int q = 0; q < rows; ++q)
+      bulk_load(slots + ((size_t)st * R_ + q) * slot + kBandPad, field + (size_t)(r0 + q) * pitch,
+                rowbytes, &full[st]);
+  };
+  if (t == 0)
+    for (int st = 0; st < S; ++st) {
+      const long long grp = blockIdx.x + (long long)st * gridDim.x;
+      if (grp < ngroups) issue(grp, st);
+    }
+
+  int it = 0;
+  bool failed = false;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+    const int st = it % S;
+    const bool ok = mbar_wait_bounded(&full[st], (uint32_t)(it / S) & 1u, kWaitLimitNs);
+    E* tile = slots + (size_t)st * R_ * slot + kBandPad;
+    const long long r0 = grp * R_;
+    const int rows = (int)min((long long)R_, nrows - r0);
+    if (ok && worker) {
+      E* sp = tile + (size_t)rr * slot + x0;
+      for (int q = rr; q < rows; q += rp, sp += (size_t)rp * slot) {
+        const R vr = __ldg(vyz + r0 + q);
+        float4 raw = *reinterpret_cast<float4*>(sp);
+        E* ev = reinterpret_cast<E*>(&raw);
+        if (!edge) {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e)
+            ev[e] = F::pointwise(F::scaled(ev[e], s), vxr[e] + vr, dt, g);
+          *reinterpret_cast<float4*>(sp) = raw;
+        } else {
+          E* row = sp - x0;
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            const int x = x0 + e;
+            if (x < nx) {
+              const E v = F::pointwise(F::scaled(ev[e], s), vxr[e] + vr, dt, g);
+              const E mv = F::scaled(v, R(-1));
+              row[x] = v;
+              if (x <= kBandPad - 2) row[-2 - x] = mv;          // image about -1
+              if (x > nx - kBandPad) row[2 * nx - x] = mv;      // image about nx
+            } else if (x == nx) {
+              row[x] = F::zero();                                // the ghost
+            }
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (worker) {
+      const E* sp = tile + (size_t)rr * slot + x0 - H * EPT;
+      E* gp = field + (size_t)(r0 + rr) * pitch + x0;
+      for (int q = rr; q < rows; q += rp, sp += (size_t)rp * slot, gp += (size_t)rp * pitch) {
+        float4 wv[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) wv[v] = reinterpret_cast<const float4*>(sp)[v];
+        const E* win = reinterpret_cast<const E*>(wv);
+        float4 ov;
+        E* o = reinterpret_cast<E*>(&ov);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const int c = H * EPT + e;   // the output's position in the window
+          E acc = F::mul(wt[W], win[c]);
+#pragma unroll
+          for (int k = 1; k <= W; ++k) acc = F::chain(wt[W + k], F::add(win[c - k], win[c + k]), acc);
+          o[e] = acc;
+        }
+        if (x0 + EPT <= nx) {
+          *reinterpret_cast<float4*>(gp) = ov;
+        } else {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e)
+            if (x0 + e < nx) gp[e] = o[e];
+        }
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      const long long nxt = grp + (long long)S * gridDim.x;
+      if (nxt < ngroups) {
+        fence_smem_to_async();
+        issue(nxt, st);
+      }
+    }
+  }
+  if (failed && t == 0) {
+    atomicOr(p.status, kStatusTimeout);
+    // wait (bounded) for every copy still in flight before the block exits
+    for (int q = 0; q < S; ++q) {
+      const int it2 = it + q;
+      const long long grp2 = blockIdx.x + (long long)it2 * gridDim.x;
+      if (grp2 < ngroups) mbar_wait_bounded(&full[it2 % S], (uint32_t)(it2 / S) & 1u, kWaitLimitNs);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 
 template <class R>
@@ -815,6 +994,40 @@ int stream_warps_per_sm(int axis, bool complex_field, int trunc) {
     case 8: return stream_warps_per_sm_L<8>(axis, complex_field);
     default: return 4;
   }
+}
+
+template <int W> static auto band_kernel(bool cplx) {
+  return cplx ? k_sweep_x_band<float, true, W> : k_sweep_x_band<float, false, W>;
+}
+
+static void (*band_kernel_for(int w, bool cplx))(SweepParams) {
+  switch (w) {
+    case 3: return band_kernel<3>(cplx);
+    case 5: return band_kernel<5>(cplx);
+    case 8: return band_kernel<8>(cplx);
+    default: return nullptr;
+  }
+}
+
+size_t x_band_smem(const SweepParams& p, bool complex_field) {
+  return 128 + (size_t)p.band_stages * p.band_rows * (p.pitch + 2 * kBandPad) *
+                   (complex_field ? 8 : 4);
+}
+
+cudaError_t x_band_prepare(int w, bool complex_field, int threads, size_t smem,
+                           int* blocks_per_sm) {
+  void (*k)(SweepParams) = band_kernel_for(w, complex_field);
+  if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
+}
+
+cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int grid,
+                                cudaStream_t st) {
+  void (*k)(SweepParams) = band_kernel_for(p.band_w, complex_field);
+  if (!k) return cudaErrorInvalidValue;
+  return launch_pdl(k, grid, p.band_threads, x_band_smem(p, complex_field), st, p);
 }
 
 cudaError_t launch_sweep_fast(int axis, const SweepParams& p, bool complex_field, int grid,

@@ -232,7 +232,10 @@ def gp_get_info(h) -> dict:
     _check(load_library().gp_get_info(h, v), h)
     keys = ("pitch", "is_complex", "lines_x", "lines_y", "lines_z", "bytes", "fast_mask",
             "trunc")
-    return dict(zip(keys, list(v)))
+    d = dict(zip(keys, list(v)))
+    d["band_w"] = (d["fast_mask"] >> 4) & 15 if d["fast_mask"] & 8 else 0
+    d["fast_mask"] &= 15
+    return d
 
 
 def gp_observables_noalloc(psi_ptr: int, nx: int, ny: int, nz: int, pitch: int, prec: int,

@@ -314,11 +314,11 @@ FAST_SHAPES = [(64, 48, 32), (37, 29, 23), (240, 20, 16), (300, 40, 30), (17, 33
 @pytest.mark.parametrize("shape", FAST_SHAPES)
 @pytest.mark.parametrize("mode", ["imag", "real"])
 def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mode, g, monkeypatch):
-    """The FP32 sweeps that cut the decaying coupling at depth L (|B|^(L+1) <= 2^-30)
-    agree with the exact FP32 tile kernels to FP32 rounding, and both with the FP64
-    oracle.  g = 50 keeps the nonlinear phase per step near the 1/16 switch of the
-    small-argument polynomials (both branches run); g = 3000 takes the library
-    exp / sincos."""
+    """The FP32 sweeps that cut the decaying coupling (the banded x operator with
+    neglected entries <= 2^-28 per row; the y / z recurrences at depth L with
+    |B|^(L+1) <= 2^-30) agree with the streaming x recurrence and with the exact FP32
+    tile kernels to FP32 rounding, and all of them with the FP64 oracle.  g = 50 keeps
+    the nonlinear phase per step small; g = 3000 makes it about 0.25 per step."""
     p = problem(orc, *shape, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=g, hy=0.18, hz=0.22)
     steps = 20
     if mode == "imag":
@@ -328,11 +328,11 @@ def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mod
         psi0 = orc.step_imag(p, orc.init_gaussian(p), 10).astype(complex)
         ref = orc.step_real(p, psi0, steps)
     outs = {}
-    for kind in ("auto", "tile"):
-        if kind == "tile":
-            monkeypatch.setenv("GP_SWEEP_KERNELS", "tile")
-        else:
+    for kind in ("auto", "stream", "tile"):
+        if kind == "auto":
             monkeypatch.delenv("GP_SWEEP_KERNELS", raising=False)
+        else:
+            monkeypatch.setenv("GP_SWEEP_KERNELS", kind)
         s = solver(P, p, prec="f32")
         s.set_psi(psi0)
         if mode == "imag":
@@ -344,11 +344,17 @@ def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mod
         s.close()
     monkeypatch.delenv("GP_SWEEP_KERNELS", raising=False)
     assert outs["tile"][1]["fast_mask"] == 0
+    assert outs["stream"][1]["band_w"] == 0
     if shape[0] >= 16:
-        assert outs["auto"][1]["fast_mask"] == 7, outs["auto"][1]
+        assert (outs["auto"][1]["fast_mask"] & 7) == 7, outs["auto"][1]
+        assert (outs["stream"][1]["fast_mask"] & 7) == 7, outs["stream"][1]
+    # h = 0.2, dt = 0.004: a = 0.025 (imaginary) and 0.025 i both need half-width 5;
+    # rows shorter than 8 points keep the streaming x kernel
+    assert outs["auto"][1]["band_w"] == (0 if shape[0] < 8 else 5), outs["auto"][1]
     # FP32 rounding, amplified by the nonlinear phase (dt g |psi|^2 ~ 0.25 per step at
     # g = 3000) over 20 steps: measured up to 3.1e-6 of max|psi| at g = 3000
     tol = (3e-6 if g < 1000 else 1e-5) * np.max(np.abs(ref))
     for kind in outs:
         assert np.max(np.abs(outs[kind][0] - ref)) <= tol, kind
     assert np.max(np.abs(outs["auto"][0] - outs["tile"][0])) <= tol
+    assert np.max(np.abs(outs["stream"][0] - outs["tile"][0])) <= tol
