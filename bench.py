@@ -244,10 +244,12 @@ def run_cuda(args):
     rt = "float" if sbytes == 4 else "double"
     L = info["trunc"]
     kernels = {
-        "sweep_x": (f"k_sweep_x_band<float,false,{info['band_w']}>" if info["band_w"] else
+        "sweep_x": (f"k_sweep_x_band<float,false,{info['band_w']}>" if info["band_mask"] & 1 else
                     f"k_sweep_x_stream<float,false,{L}>" if info["fast_mask"] & 1 else f"k_sweep_x<{rt},false>"),
-        "sweep_y": f"k_sweep_stream<float,false,1,false,{L}>" if info["fast_mask"] & 2 else f"k_sweep_y<{rt},false>",
-        "sweep_z": f"k_sweep_stream<float,false,2,true,{L}>" if info["fast_mask"] & 4 else f"k_sweep_z<{rt},false,true>"}
+        "sweep_y": (f"k_sweep_band_line<float,false,1,false,{info['band_w']}>" if info["band_mask"] & 2 else
+                    f"k_sweep_stream<float,false,1,false,{L}>" if info["fast_mask"] & 2 else f"k_sweep_y<{rt},false>"),
+        "sweep_z": (f"k_sweep_band_line<float,false,2,true,{info['band_w']}>" if info["band_mask"] & 4 else
+                    f"k_sweep_stream<float,false,2,true,{L}>" if info["fast_mask"] & 4 else f"k_sweep_z<{rt},false,true>")}
     per = {}
     for i, n in enumerate(names):
         # (kernel name recorded per sweep)

@@ -179,10 +179,13 @@ int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]);
  *   info[2..4] lines per shared-memory tile of the x / y / z tile kernels,
  *   info[5] device bytes in use,
  *   info[6] bit a set when sweep a (0 x, 1 y, 2 z) uses the FP32 kernels without
- *           shared-memory tiles (truncated decaying coupling, see gp_sweeps.cu),
- *   info[7] their truncation depth L (0 when none is used).
+ *           shared-memory line tiles (decaying coupling cut below FP32 rounding, see
+ *           gp_sweeps.cu), bit 3 + a when that kernel is the banded operator, bits
+ *           8..11 the largest band half-width W,
+ *   info[7] the truncation depth L of the streaming recurrences (0 when none).
  * GP_SWEEP_KERNELS=tile in the environment at gp_create time makes every sweep
- * use the tile kernels.                                                          */
+ * use the tile kernels; =stream keeps the FP32 sweeps on the streaming recurrences
+ * (=stream_x, =stream_yz: only x, only y and z).                                 */
 int gp_get_info(const gp_solver* s, long long info[8]);
 
 /* Observables of a field that sits in the caller's own device memory, computed

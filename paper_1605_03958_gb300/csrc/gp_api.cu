@@ -40,8 +40,8 @@ constexpr size_t kFastTileBytes = 100 * 1024;   // preferred tile: >= 2 blocks p
 constexpr size_t kMaxTileBytes = 226 * 1024;    // opt-in shared memory per block, minus slack
 constexpr int kBandHalfMax = 8;                 // band half-widths 3, 5 or 8
 constexpr int kBandMinNx = 8;                   // one reflection covers every window
-constexpr size_t kBandStageBytes = 16 * 1024;   // target bytes of one group of the x band kernel
-constexpr int kBandStages = 3;
+constexpr int kBandStages = 3;                  // rows in flight per warp of the x band kernel
+constexpr size_t kBandBlockBytes = 100 * 1024;  // above this, 2 stages
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -60,7 +60,8 @@ struct Layout {
   size_t off_field = 0, off_staging = 0, off_coef = 0, off_vtab = 0, off_otab = 0;
   size_t off_partials = 0, off_scalars = 0, total = 0;
   size_t coef_off[2][3][2] = {};   // [mode][axis][A/B] byte offset from off_coef
-  size_t vyz_off = 0;              // FP32: V_y[j] + V_z[k] per row, from off_coef
+  size_t fx_off[2] = {};           // FP32 trap factors along x per mode [pitch], from off_coef
+  size_t fyz_off[2] = {};          // FP32 trap factor per row per mode, from off_coef
   size_t npartials = 0;
   SweepGeom geom[2][3];
   long long ntiles_z[2] = {0, 0};
@@ -157,10 +158,13 @@ const char* compute_layout(const gp_params* p, Layout* L) {
         L->coef_off[m][a][ab] = c;
         c = align_up(c + (size_t)n[a] * L->rbytes * (m + 1), kAlign);
       }
-  if (L->rbytes == 4) {
-    L->vyz_off = c;
-    c = align_up(c + rows * 4, kAlign);
-  }
+  if (L->rbytes == 4)
+    for (int m = 0; m < 2; ++m) {
+      L->fx_off[m] = c;
+      c = align_up(c + (size_t)L->pitch[m] * 4 * (m + 1), kAlign);
+      L->fyz_off[m] = c;
+      c = align_up(c + rows * 4 * (m + 1), kAlign);
+    }
   off = align_up(off + c, kAlign);
   L->off_vtab = off;
   off = align_up(off + (size_t)(p->nx + p->ny + p->nz) * L->rbytes, kAlign);
@@ -193,16 +197,20 @@ void cn_coefficients(int n, std::complex<double> a, std::vector<std::complex<dou
 }
 
 // GP_SWEEP_KERNELS=tile makes every sweep use the shared-memory tile kernels;
-// GP_SWEEP_KERNELS=stream keeps the FP32 x sweep on the streaming recurrence kernel
-// instead of the banded one (diagnostics and A/B measurements); any other value or
-// none: automatic choice.
+// GP_SWEEP_KERNELS=stream keeps the FP32 sweeps on the streaming recurrence kernels
+// instead of the banded ones (stream_x: only x, stream_yz: only y and z); for
+// diagnostics and A/B measurements.  Any other value or none: automatic choice.
 bool force_tile() {
   const char* v = std::getenv("GP_SWEEP_KERNELS");
   return v && std::strcmp(v, "tile") == 0;
 }
 bool force_stream() {
   const char* v = std::getenv("GP_SWEEP_KERNELS");
-  return v && std::strcmp(v, "stream") == 0;
+  return v && (std::strcmp(v, "stream") == 0 || std::strcmp(v, "stream_x") == 0);
+}
+bool force_stream_yz() {
+  const char* v = std::getenv("GP_SWEEP_KERNELS");
+  return v && (std::strcmp(v, "stream") == 0 || std::strcmp(v, "stream_yz") == 0);
 }
 
 // Row of the free-line CN operator T_inf = (I + aK)^{-1} (I - aK) (K the second
@@ -284,8 +292,8 @@ struct gp_solver {
   int head[2][3] = {};               // see SweepParams::head
   int trunc[2][3] = {};              // FP32 fast sweeps: truncation depth, 0 = use the tile kernel
   int fast_grid[2][3] = {};          // blocks of the fast sweeps (x band: persistent grid)
-  int band_w[2] = {};                // FP32 banded x sweep half-width per mode, 0 = not used
-  float band_wt[2][2 * 17] = {};     // its weights per mode (complex: pairs)
+  int band_w[2][3] = {};             // FP32 banded sweep half-width per mode and axis, 0 = not used
+  float band_wt[2][3][2 * 17] = {};  // its weights (complex: pairs)
   int nsm = 0;
   CUtensorMap tmap[2][3];  // [mode][axis]; axis 0 unused (64-byte aligned type)
   // timing
@@ -438,30 +446,62 @@ void fill_sweep_params(gp_solver* s) {
         long long blocks = (warps + 3) / 4;   // x: capped at the resident grid by the launcher
         s->fast_grid[m][a] = (int)blocks;
       }
-      if (a == 0 && s->band_w[m]) {
-        const int ept = m == 0 ? 4 : 2;
-        const int tpr = (p.nx + ept - 1) / ept;
-        q.vyz = coef + s->L.vyz_off;
-        std::memcpy(q.band_wt, s->band_wt[m], sizeof q.band_wt);
-        q.band_w = s->band_w[m];
-        q.band_tpr = tpr;
-        q.band_threads = tpr <= 256 ? 256 : (tpr + 31) / 32 * 32;
-        q.band_rp = q.band_threads / tpr;
+      if (a == 0 && s->band_w[m][0]) {
+        q.band_fx = coef + s->L.fx_off[m];
+        q.band_fyz = coef + s->L.fyz_off[m];
+        std::memcpy(q.band_wt, s->band_wt[m][0], sizeof q.band_wt);
+        q.band_w = s->band_w[m][0];
         const size_t slot_bytes = ((size_t)s->L.pitch[m] + 16) * rb * (m + 1);
-        const int passes = std::max<int>(1, (int)(kBandStageBytes / (slot_bytes * q.band_rp)));
-        q.band_rows = q.band_rp * passes;
-        q.band_stages = kBandStages;
+        q.band_stages = gpk::kBandWarps * kBandStages * slot_bytes <= kBandBlockBytes ? kBandStages : 2;
         const size_t smem = gpk::x_band_smem(q, m == 1);
         int bps = 0;
-        const long long groups = ((long long)p.ny * p.nz + q.band_rows - 1) / q.band_rows;
-        if (gpk::x_band_prepare(q.band_w, m == 1, q.band_threads, smem, &bps) == cudaSuccess &&
-            bps > 0) {
-          s->fast_grid[m][0] = (int)std::min<long long>(groups, (long long)s->nsm * bps);
+        if (gpk::x_band_prepare(q.band_w, m == 1, smem, &bps) == cudaSuccess && bps > 0) {
+          // rows per warp such that every warp is resident at once with equal work
+          const long long rows = (long long)p.ny * p.nz;
+          const long long cap = (long long)s->nsm * bps * gpk::kBandWarps;
+          q.band_rows = (int)((rows + cap - 1) / cap);
+          const long long warps = (rows + q.band_rows - 1) / q.band_rows;
+          s->fast_grid[m][0] = (int)((warps + gpk::kBandWarps - 1) / gpk::kBandWarps);
         } else {
           cudaGetLastError();
-          s->band_w[m] = 0;
+          s->band_w[m][0] = 0;
           q.band_w = 0;
         }
+      }
+      if (a > 0 && s->band_w[m][a]) {
+        std::memcpy(q.band_wt, s->band_wt[m][a], sizeof q.band_wt);
+        q.band_w = s->band_w[m][a];
+        q.psi = a == 1 ? (void*)s->field : (void*)s->staging;
+        q.out = a == 1 ? (void*)s->staging : (void*)s->field;
+        // segment length: a multiple of the ring length 2W+1 that best fills whole waves
+        // of resident threads, charging each segment its 2W halo loads at a third of
+        // an output's cost
+        const int P = 2 * q.band_w + 1;
+        const int ept = m == 0 ? 4 : 2;
+        const long long cols = (long long)((p.nx + ept - 1) / ept) * (a == 1 ? p.nz : p.ny);
+        const int bps = std::max(1, gpk::band_line_blocks_per_sm(a, m == 1, q.band_w));
+        const long long cap = (long long)s->nsm * bps * 128;
+        int best_seg = P;
+        double best = -1.0;
+        for (int mu = 1; mu * P <= std::max(n[a], P) && mu <= 16; ++mu) {
+          const int seg = mu * P;
+          const long long items = cols * ((n[a] + seg - 1) / seg);
+          const long long waves = (items + cap - 1) / cap;
+          const double fill = (double)items / (double)(waves * cap);
+          const double eff = fill * seg / (seg + 2.0 * q.band_w / 3.0);
+          if (eff > best * 1.02) {
+            best = eff;
+            best_seg = seg;
+          }
+        }
+        // one FP64 norm partial per block must fit the partials area
+        long long blocks = 0;
+        for (;; best_seg += P) {
+          blocks = (cols * ((n[a] + best_seg - 1) / best_seg) + 127) / 128;
+          if (blocks <= (long long)s->L.npartials || best_seg >= n[a]) break;
+        }
+        q.band_seg = best_seg;
+        s->fast_grid[m][a] = (int)blocks;
       }
     }
 }
@@ -525,33 +565,37 @@ int upload_tables(gp_solver* s) {
         }
       }
     }
-  // FP32 x sweep as a banded operator on the odd extension of each row, when a
-  // half-width <= 8 is exact to FP32 rounding and a row fits one block
-  for (int m = 0; m < 2; ++m) {
-    s->band_w[m] = 0;
-    const int ept = m == 0 ? 4 : 2;
-    if (f64 || force_tile() || force_stream() || p.nx < kBandMinNx ||
-        (p.nx + ept - 1) / ept > gpk::kBandMaxThreads)
-      continue;
-    const double beta = p.dt / (4.0 * h[0] * h[0]);
-    std::vector<std::complex<double>> w;
-    const int W = cn_free_row(m == 0 ? std::complex<double>(beta, 0.0)
-                                     : std::complex<double>(0.0, beta), &w);
-    if (!W) continue;
-    s->band_w[m] = W;
-    for (int k = 0; k <= 2 * W; ++k) {
-      if (m == 0) {
-        s->band_wt[m][k] = (float)w[k].real();
-      } else {
-        s->band_wt[m][2 * k] = (float)w[k].real();
-        s->band_wt[m][2 * k + 1] = (float)w[k].imag();
+  // FP32 sweeps as banded operators on the odd extension of each line, when a
+  // half-width <= 8 is exact to FP32 rounding and the line has >= kBandMinNx points
+  for (int m = 0; m < 2; ++m)
+    for (int a = 0; a < 3; ++a) {
+      s->band_w[m][a] = 0;
+      if (f64 || force_tile() || n[a] < kBandMinNx) continue;
+      if (force_stream() && a == 0) continue;
+      if (force_stream_yz() && a > 0) continue;
+      const double beta = p.dt / (4.0 * h[a] * h[a]);
+      std::vector<std::complex<double>> w;
+      const int W = cn_free_row(m == 0 ? std::complex<double>(beta, 0.0)
+                                       : std::complex<double>(0.0, beta), &w);
+      if (!W) continue;
+      s->band_w[m][a] = W;
+      w[W] -= 1.0;   // the kernels add the identity part separately
+      for (int k = 0; k <= 2 * W; ++k) {
+        if (m == 0) {
+          s->band_wt[m][a][k] = (float)w[k].real();
+        } else {
+          s->band_wt[m][a][2 * k] = (float)w[k].real();
+          s->band_wt[m][a][2 * k + 1] = (float)w[k].imag();
+        }
       }
     }
-  }
-  // the FP32 y / z kernels write out of place (y: field -> staging, z: staging ->
-  // field), so they are used together or not at all
+  // the FP32 y / z kernels (banded or streaming) write out of place (y: field ->
+  // staging, z: staging -> field), so they are used together or not at all
   for (int m = 0; m < 2; ++m)
-    if (!s->trunc[m][1] || !s->trunc[m][2]) s->trunc[m][1] = s->trunc[m][2] = 0;
+    if (!(s->trunc[m][1] || s->band_w[m][1]) || !(s->trunc[m][2] || s->band_w[m][2])) {
+      s->trunc[m][1] = s->trunc[m][2] = 0;
+      s->band_w[m][1] = s->band_w[m][2] = 0;
+    }
   // potential tables V_a(x) = w_a^2 x^2 / 2 in storage precision, and FP64 copies + x^2
   const size_t vt = L.off_vtab - L.off_coef, ot = L.off_otab - L.off_coef;
   size_t iv = 0;
@@ -564,17 +608,29 @@ int upload_tables(gp_solver* s) {
       put<double>(buf, ot + iv * 8, V);
       put<double>(buf, ot + (ntot + iv) * 8, x * x);
     }
-  // FP32: the trap's y + z part per row, summed in FP32 from the FP32 tables exactly as
-  // the kernels that read V_y and V_z separately do
-  if (!f64)
+  // FP32: trap factors of the pointwise substep, exp(-dt V) (real field) and
+  // cis(-dt V) = (cos dt V, -sin dt V) (complex field), separable as a factor along x
+  // and one per row; computed in FP64, rounded once
+  if (!f64) {
+    auto pot = [&](int a, int i) {
+      const double x = (i - 0.5 * (n[a] - 1)) * h[a];
+      return 0.5 * w[a] * w[a] * x * x;
+    };
+    for (int i = 0; i < p.nx; ++i) {
+      const double th = p.dt * pot(0, i);
+      put<float>(buf, L.fx_off[0] + (size_t)i * 4, (float)std::exp(-th));
+      put<float>(buf, L.fx_off[1] + (size_t)i * 8, (float)std::cos(th));
+      put<float>(buf, L.fx_off[1] + (size_t)i * 8 + 4, (float)-std::sin(th));
+    }
     for (int k = 0; k < p.nz; ++k)
       for (int j = 0; j < p.ny; ++j) {
-        float vy, vz;
-        std::memcpy(&vy, buf.data() + vt + (size_t)(p.nx + j) * 4, 4);
-        std::memcpy(&vz, buf.data() + vt + (size_t)(p.nx + p.ny + k) * 4, 4);
-        const float sum = vy + vz;
-        put<float>(buf, L.vyz_off + ((size_t)k * p.ny + j) * 4, sum);
+        const double th = p.dt * (pot(1, j) + pot(2, k));
+        const size_t r = (size_t)k * p.ny + j;
+        put<float>(buf, L.fyz_off[0] + r * 4, (float)std::exp(-th));
+        put<float>(buf, L.fyz_off[1] + r * 8, (float)std::cos(th));
+        put<float>(buf, L.fyz_off[1] + r * 8 + 4, (float)-std::sin(th));
       }
+  }
   GP_CUDA(s, cudaMemcpyAsync(s->base + L.off_coef, buf.data(), span, cudaMemcpyHostToDevice,
                              s->stream));
   GP_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -708,6 +764,8 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
   cudaError_t e;
   if (axis == 0 && q.band_w)
     e = gpk::launch_sweep_x_band(q, m == 1, s->fast_grid[m][0], s->stream);
+  else if (q.band_w)
+    e = gpk::launch_sweep_band_line(axis, q, m == 1, s->fast_grid[m][axis], s->stream);
   else if (q.trunc)
     e = gpk::launch_sweep_fast(axis, q, m == 1, s->fast_grid[m][axis], s->stream);
   else if (axis == 0)
@@ -979,8 +1037,14 @@ int gp_get_info(const gp_solver* s, long long info[8]) {
   info[3] = s->L.geom[m][1].lines;
   info[4] = s->L.geom[m][2].lines;
   info[5] = (long long)s->L.total;
-  info[6] = (s->trunc[m][0] ? 1 : 0) | (s->trunc[m][1] ? 2 : 0) | (s->trunc[m][2] ? 4 : 0) |
-            (s->band_w[m] ? 8 | (s->band_w[m] << 4) : 0);
+  info[6] = 0;
+  int wmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (s->trunc[m][a] || s->band_w[m][a]) info[6] |= 1 << a;
+    if (s->band_w[m][a]) info[6] |= 8 << a;
+    wmax = std::max(wmax, s->band_w[m][a]);
+  }
+  info[6] |= (long long)wmax << 8;
   info[7] = std::max(s->trunc[m][0], std::max(s->trunc[m][1], s->trunc[m][2]));
   return GP_OK;
 }

@@ -21,9 +21,8 @@ constexpr int kMaxExtent = 2048;
 // Longest line segment one TMA box covers (hardware limit on a box dimension).
 constexpr int kMaxBox = 256;
 
-// Largest block of the banded FP32 x sweep (threads per row = nx / elements per
-// 16-byte vector must fit it).
-constexpr int kBandMaxThreads = 512;
+// Warps per block of the banded FP32 x sweep (each warp works on its own rows).
+constexpr int kBandWarps = 4;
 
 // Fixed launch shape of the reductions, so that their summation order (and hence
 // their result) does not depend on the device.
@@ -55,14 +54,13 @@ struct SweepParams {
   int trunc;             // FP32 fast sweeps: truncation depth L of the decaying coupling
   int nseg;              // FP32 fast y / z sweeps: segments per line
   // FP32 banded x sweep (band_w > 0)
-  const void* vyz;       // V_y[j] + V_z[k] per row r = k ny + j, FP32
-  float band_wt[2 * 17]; // free-line CN row w_{k - band_w}, k = 0 .. 2 band_w (complex: pairs)
+  const void* band_fx;   // trap factors along x: exp(-dt V_x) or cis(-dt V_x), [pitch], FP32
+  const void* band_fyz;  // trap factor per row r = k ny + j: exp(-dt (V_y + V_z)) or cis(..)
+  float band_wt[2 * 17]; // free-line CN row w_{k - band_w}, k = 0 .. 2 band_w, centre as w_0 - 1 (complex: pairs)
   int band_w;            // half-width W of the band (3, 5 or 8)
-  int band_threads;      // block size
-  int band_tpr;          // threads per row: ceil(nx / elements per 16-byte vector)
-  int band_rp;           // rows handled at once by the block (band_threads / band_tpr)
-  int band_rows;         // rows per group (one stage of shared memory)
-  int band_stages;       // groups in flight per block
+  int band_rows;         // x: consecutive rows per warp
+  int band_stages;       // x: rows in flight per warp
+  int band_seg;          // y / z: points per line segment (a multiple of 2 band_w + 1)
   // pointwise substep (x sweep only)
   const void* vx;
   const void* vy;
@@ -103,13 +101,16 @@ template <class R> cudaError_t sweep_set_smem_limits(size_t max_smem);
 // y, z: streaming, one lane per line); y / z grid in blocks of 128 threads.
 cudaError_t launch_sweep_fast(int axis, const SweepParams& p, bool complex_field, int grid,
                               cudaStream_t st);
-// FP32 banded x sweep: dynamic shared memory of a block, one-time preparation
-// (shared-memory limit, resident blocks per SM) and launch on `grid` persistent blocks.
+// FP32 banded x sweep: dynamic shared memory of a block of kBandWarps warps, one-time
+// preparation (shared-memory limit, resident blocks per SM) and launch on `grid` blocks.
 size_t x_band_smem(const SweepParams& p, bool complex_field);
-cudaError_t x_band_prepare(int w, bool complex_field, int threads, size_t smem,
-                           int* blocks_per_sm);
+cudaError_t x_band_prepare(int w, bool complex_field, size_t smem, int* blocks_per_sm);
 cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int grid,
                                 cudaStream_t st);
+// FP32 banded y / z sweeps (out of place like the streaming ones), blocks of 128 threads.
+cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_field, int grid,
+                                   cudaStream_t st);
+int band_line_blocks_per_sm(int axis, bool complex_field, int w);
 // Resident warps per SM of the streaming y / z kernel (occupancy calculator).
 int stream_warps_per_sm(int axis, bool complex_field, int trunc);
 

@@ -67,6 +67,18 @@ template <class R> struct Field<R, false> {
   static __device__ __forceinline__ E mul(E a, E b) { return a * b; }
   static __device__ __forceinline__ E add(E a, E b) { return a + b; }
   static __device__ __forceinline__ R abs2(E v) { return v * v; }
+  // v f exp(-y) with f = exp(-dt V) from the separable trap tables and y = dt g v^2:
+  // for |y| <= 1/16 exp(-y) by its Taylor polynomial of degree 4 (remainder below
+  // |y|^5/120 < 1e-8, under FP32 rounding), else by the library exp
+  static __device__ __forceinline__ E nonlinear_small(E v, E f, R y) {
+    const R z = -y;
+    R q = fma(z, R(1.0 / 24.0), R(1.0 / 6.0));
+    q = fma(z, q, R(0.5));
+    q = fma(z, q, R(1));
+    q = fma(z, q, R(1));
+    return v * f * q;
+  }
+  static __device__ __forceinline__ E nonlinear_full(E v, E f, R y) { return v * f * gp_exp(-y); }
 };
 
 // Complex field, real time.
@@ -88,6 +100,20 @@ template <class R> struct Field<R, true> {
   static __device__ __forceinline__ E mul(E a, E b) { return cmul(a, b); }
   static __device__ __forceinline__ E add(E a, E b) { return cadd(a, b); }
   static __device__ __forceinline__ R abs2(E v) { return fma(v.x, v.x, v.y * v.y); }
+  // v f (cos th - i sin th) with f = cis(-dt V) from the separable trap tables and
+  // th = dt g |v|^2: for |th| <= 1/16 cos and sin by their Taylor polynomials of
+  // degrees 4 and 5 (remainders below th^6/720 and th^7/5040), else the library sincos
+  static __device__ __forceinline__ E nonlinear_small(E v, E f, R th) {
+    const R t2 = th * th;
+    const R cs = fma(t2, fma(t2, R(1.0 / 24.0), R(-0.5)), R(1));
+    const R sn = th * fma(t2, fma(t2, R(1.0 / 120.0), R(-1.0 / 6.0)), R(1));
+    return cmul(cmul(v, f), E{cs, -sn});
+  }
+  static __device__ __forceinline__ E nonlinear_full(E v, E f, R th) {
+    R sn, cs;
+    gp_sincos(th, &sn, &cs);
+    return cmul(cmul(v, f), E{cs, -sn});
+  }
 };
 
 template <class E>
@@ -748,21 +774,25 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
 // a long line and picks the smallest W in {3, 5, 8} whose neglected entries sum to at
 // most 2^-28.  Every output is then the same (2W+1)-tap dot product (weights in the
 // kernel parameters), with no recurrence and no per-index coefficients: all the
-// elements of a row are computed at once.
+// elements of a row are computed at once.  The centre weight is stored as w_0 - 1 and
+// the identity part added last, u_j = v_j + [(w_0 - 1) v_j + sum_k w_k (v_{j-k} +
+// v_{j+k})]: the bracket is small (|w_0 - 1| and |w_k| are O(a)), so rounding the
+// weights to FP32 perturbs u far below an FP32 ulp of it, and the same perturbation,
+// repeated every step, does not build up a drift.
 //
-// A block is persistent over groups of band_rows consecutive rows.  Each row of a
-// group arrives by one bulk copy into a shared-memory slot with kBandPad elements of
-// room on both sides; band_stages groups are in flight.  Thread t serves the EPT
-// elements (one 16-byte vector) from x0 = EPT (t mod tpr) of rows t / tpr,
-// t / tpr + rp, ... of the group.  Per group: the pending scale and the pointwise
-// substep in shared memory, the threads at the ends of a row also writing the odd
-// images into the pads (zero at the ghosts); a block barrier; the dot products from
-// 16-byte shared loads; stores straight to the field (in place: a block owns its
-// rows).  Needs nx >= kBandPad so that one reflection covers every window.
-constexpr int kBandPad = 8;   // room for the odd images on each side of a row slot
+// Each warp owns band_rows consecutive rows (the host sizes this so that all warps
+// are resident at once) and works on them alone, with warp barriers only.  A row
+// arrives by one bulk copy into a shared-memory slot with kBandPad elements of room
+// on both sides; band_stages rows are in flight per warp.  Lane l serves the 16-byte
+// vectors l, l + 32, ... of the row (EPT elements each).  Per row: the pending scale
+// and the pointwise substep in place; then the odd images of the first and last 7
+// elements into the pads and zero at the ghosts; then the dot products from 16-byte
+// shared loads, stored straight to the field (in place: a warp owns its rows).
+// Needs nx >= kBandPad so that one reflection covers every window.
+constexpr int kBandPad = 8;     // room for the odd images on each side of a row slot
 
 template <class R, bool CPLX, int W>
-__global__ void __launch_bounds__(kBandMaxThreads) k_sweep_x_band(const __grid_constant__ SweepParams p) {
+__global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_constant__ SweepParams p) {
   using F = Field<R, CPLX>;
   using E = typename F::E;
   constexpr int EPT = 16 / (int)sizeof(E);   // elements per 16-byte vector
@@ -770,144 +800,217 @@ __global__ void __launch_bounds__(kBandMaxThreads) k_sweep_x_band(const __grid_c
   constexpr int NV = 2 * H + 1;              // vectors in a window
   static_assert(H * EPT <= kBandPad, "window inside the slot");
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  E* slots = reinterpret_cast<E*>(smem + 128);
-  const int nx = p.nx, pitch = p.pitch;
+  const int nx = p.nx, pitch = p.pitch, S = p.band_stages, RPW = p.band_rows;
   const int slot = pitch + 2 * kBandPad;
-  const int R_ = p.band_rows, S = p.band_stages, tpr = p.band_tpr, rp = p.band_rp;
-  const int t = threadIdx.x;
-  const int rr = t / tpr;
-  const int x0 = (t - rr * tpr) * EPT;
-  const bool worker = rr < rp;
-  // threads whose elements have odd images in the pads, or run past nx
-  const bool edge = x0 <= kBandPad - 2 || x0 + EPT - 1 > nx - kBandPad;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
+  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * slot + kBandPad;
   const long long nrows = (long long)p.ny * p.nz;
-  const long long ngroups = (nrows + R_ - 1) / R_;
+  const long long row0 = ((long long)blockIdx.x * kBandWarps + wib) * RPW;
+  const int nrow = (int)max(0LL, min((long long)RPW, nrows - row0));
+  const int nvec = (nx + EPT - 1) / EPT;
   E* field = static_cast<E*>(p.psi);
   const E* wt = reinterpret_cast<const E*>(p.band_wt);   // w_{k-W}, k = 0 .. 2W
-
-  if (t == 0)
-    for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
-  // the ghost positions -1 and pitch (= nx when nx == pitch) stay zero
-  for (int q = t; q < S * R_; q += blockDim.x) {
-    E* sl = slots + (size_t)q * slot + kBandPad;
-    sl[-1] = F::zero();
-    sl[pitch] = F::zero();
-  }
-  R vxr[EPT];
-  {
-    const R* vx = static_cast<const R*>(p.vx);
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) vxr[e] = (worker && x0 + e < nx) ? __ldg(vx + x0 + e) : R(0);
-  }
-  __syncthreads();
-  pdl_begin();
-  const R s = (R)(*p.scale);
-  const R dt = (R)p.dt, g = (R)p.g;
-  const R* vyz = static_cast<const R*>(p.vyz);
+  const float4* fx = static_cast<const float4*>(p.band_fx);   // trap factors along x
+  const E* fyz = static_cast<const E*>(p.band_fyz);            // trap factor per row
   const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
 
-  // group grp -> stage st: one bulk copy per row
-  auto issue = [&](long long grp, int st) {
-    const long long r0 = grp * R_;
-    const int rows = (int)min((long long)R_, nrows - r0);
-    mbar_arrive_expect_tx(&full[st], (uint32_t)rows * rowbytes);
-    for (int q = 0; q < rows; ++q)
-      bulk_load(slots + ((size_t)st * R_ + q) * slot + kBandPad, field + (size_t)(r0 + q) * pitch,
-                rowbytes, &full[st]);
+  if (lane == 0)
+    for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
+  if (lane < S) slots[(size_t)lane * slot - 1] = F::zero();   // ghost -1 of every slot
+  __syncwarp();
+  pdl_begin();
+  if (nrow == 0) return;
+  const R s = (R)(*p.scale);
+  const R dtg = (R)(p.dt * p.g);
+  auto issue = [&](int i) {   // row i of this warp -> stage i % S
+    const int st = i % S;
+    mbar_arrive_expect_tx(&full[st], rowbytes);
+    bulk_load(slots + (size_t)st * slot, field + (size_t)(row0 + i) * pitch, rowbytes, &full[st]);
   };
-  if (t == 0)
-    for (int st = 0; st < S; ++st) {
-      const long long grp = blockIdx.x + (long long)st * gridDim.x;
-      if (grp < ngroups) issue(grp, st);
-    }
+  if (lane == 0)
+    for (int i = 0; i < S && i < nrow; ++i) issue(i);
+  E f_next = fyz[row0];
 
-  int it = 0;
-  bool failed = false;
-  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
-    const int st = it % S;
-    const bool ok = mbar_wait_bounded(&full[st], (uint32_t)(it / S) & 1u, kWaitLimitNs);
-    E* tile = slots + (size_t)st * R_ * slot + kBandPad;
-    const long long r0 = grp * R_;
-    const int rows = (int)min((long long)R_, nrows - r0);
-    if (ok && worker) {
-      E* sp = tile + (size_t)rr * slot + x0;
-      for (int q = rr; q < rows; q += rp, sp += (size_t)rp * slot) {
-        const R vr = __ldg(vyz + r0 + q);
-        float4 raw = *reinterpret_cast<float4*>(sp);
-        E* ev = reinterpret_cast<E*>(&raw);
-        if (!edge) {
+  for (int i = 0; i < nrow; ++i) {
+    const int st = i % S;
+    E* row = slots + (size_t)st * slot;
+    const E fr = f_next;
+    if (i + 1 < nrow) f_next = fyz[row0 + i + 1];
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)(i / S) & 1u, kWaitLimitNs))) {
+      if (lane == 0) {
+        atomicOr(p.status, kStatusTimeout);
+        // wait (bounded) for every copy still in flight before the warp exits
+        for (int q = i; q < i + S && q < nrow; ++q)
+          mbar_wait_bounded(&full[q % S], (uint32_t)(q / S) & 1u, kWaitLimitNs);
+      }
+      __syncwarp();
+      return;
+    }
+    // pointwise substep in place (past nx too: overwritten below); the lanes of a
+    // warp take the polynomial branch together when every argument allows it
+    for (int v0 = 0; v0 < nvec; v0 += 32) {
+      const int v = v0 + lane;
+      const bool act = v < nvec;
+      float4* vp = reinterpret_cast<float4*>(row + (act ? v : 0) * EPT);
+      float4 raw = *vp;
+      const float4 fxv = __ldg(fx + (act ? v : 0));
+      E* ev = reinterpret_cast<E*>(&raw);
+      const E* fe = reinterpret_cast<const E*>(&fxv);
+      R y[EPT];
+      R ymax = R(0);
 #pragma unroll
-          for (int e = 0; e < EPT; ++e)
-            ev[e] = F::pointwise(F::scaled(ev[e], s), vxr[e] + vr, dt, g);
-          *reinterpret_cast<float4*>(sp) = raw;
-        } else {
-          E* row = sp - x0;
+      for (int e = 0; e < EPT; ++e) {
+        ev[e] = F::scaled(ev[e], s);
+        y[e] = dtg * F::abs2(ev[e]);
+        ymax = fmaxf(ymax, fabsf(y[e]));
+      }
+      if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_small(ev[e], F::mul(fe[e], fr), y[e]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_full(ev[e], F::mul(fe[e], fr), y[e]);
+      }
+      if (act) *vp = raw;
+    }
+    __syncwarp();
+    // odd images about -1 (positions -2..-8) and about nx (nx+1..nx+7), ghost nx
+    if (lane < 7) {
+      row[-2 - lane] = F::scaled(row[lane], R(-1));
+    } else if (lane < 14) {
+      const int m = lane - 7;
+      row[nx + 1 + m] = F::scaled(row[nx - 1 - m], R(-1));
+    } else if (lane == 14) {
+      row[nx] = F::zero();
+    }
+    __syncwarp();
+    E* grow = field + (size_t)(row0 + i) * pitch;
+    for (int v = lane; v < nvec; v += 32) {
+      const int x0 = v * EPT;
+      const float4* src = reinterpret_cast<const float4*>(row + x0 - H * EPT);
+      float4 wv[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) wv[q] = src[q];
+      const E* win = reinterpret_cast<const E*>(wv);
+      float4 ov;
+      E* o = reinterpret_cast<E*>(&ov);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int c = H * EPT + e;   // the output's position in the window
+        E acc = F::mul(wt[W], win[c]);
+#pragma unroll
+        for (int k = 1; k <= W; ++k) acc = F::chain(wt[W + k], F::add(win[c - k], win[c + k]), acc);
+        o[e] = F::add(win[c], acc);
+      }
+      if (x0 + EPT <= nx) {
+        *reinterpret_cast<float4*>(grow + x0) = ov;
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          if (x0 + e < nx) grow[x0 + e] = o[e];
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && i + S < nrow) {
+      fence_smem_to_async();
+      issue(i + S);
+    }
+  }
+}
+
+// y (AXIS 1) or z (AXIS 2) sweep as the banded operator on the odd extension (see the
+// x sweep above), for the FP32 field.  Thread t owns the 16-byte vector
+// xv = t mod nvec (EPT consecutive x) of one segment of band_seg points of one line;
+// consecutive threads are consecutive x, so every load and store is coalesced.  The
+// segment's outputs need its inputs plus W on each side (odd images past the line's
+// ends), held in a ring of P = 2W+1 vectors: the loop is unrolled by P, so the ring
+// slot of every tap is a compile-time constant; the P new inputs of a turn are loaded
+// together at its start, so that they are in flight at once.  Out of place (p.psi -> p.out):
+// neighbouring segments read each other's inputs.  With NORM the block also sums
+// |u|^2 (FP32 within a ring turn, FP64 across) and the last block turns the partials
+// into the renormalisation factor.
+template <class R, bool CPLX, int AXIS, bool NORM, int W>
+__global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__ SweepParams p) {
+  pdl_begin();
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  constexpr int EPT = 16 / (int)sizeof(E);
+  constexpr int P = 2 * W + 1;
+  const int nx = p.nx, n = p.n, Ls = p.band_seg;
+  const int nvec = (nx + EPT - 1) / EPT;
+  const int nother = AXIS == 1 ? p.nz : p.ny;
+  const int nseg = (n + Ls - 1) / Ls;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const E* wt = reinterpret_cast<const E*>(p.band_wt);   // w_{k-W}, k = 0 .. 2W
+  double acc = 0.0;
+  if (t < (long long)nvec * nother * nseg) {
+    const int xv = (int)(t % nvec);
+    const long long rest = t / nvec;
+    const int o = (int)(rest % nother), sg = (int)(rest / nother);
+    const size_t pitch = (size_t)p.pitch;
+    const size_t base = (AXIS == 1 ? (size_t)o * p.ny * pitch : (size_t)o * pitch) + (size_t)xv * EPT;
+    const float4* in = reinterpret_cast<const float4*>(static_cast<const E*>(p.psi) + base);
+    float4* out = reinterpret_cast<float4*>(static_cast<E*>(p.out) + base);
+    const size_t sv = (AXIS == 1 ? pitch : pitch * p.ny) * sizeof(E) / 16;   // line stride in vectors
+    const int valid = min(EPT, nx - xv * EPT);   // elements of this vector inside the field
+    const int j0 = sg * Ls, j1 = min(n, j0 + Ls);
+    const bool interior = j0 >= W && j0 + Ls + W <= n;
+    // input j of the odd extension about the ghosts -1 and n
+    auto ld = [&](int j) -> float4 {
+      if (interior || (j >= 0 && j < n)) return in[(size_t)j * sv];
+      if (j == -1 || j == n) return make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = in[(size_t)(j < 0 ? -2 - j : 2 * n - j) * sv];
+      return make_float4(-v.x, -v.y, -v.z, -v.w);
+    };
+    float4 ring[P];
+#pragma unroll
+    for (int m = 0; m < 2 * W; ++m) ring[m] = ld(j0 - W + m);
+    for (int b = j0; b < j1; b += P) {
+      float part = 0.f;
+      // the turn's P new inputs, all in flight before the first output needs one
+      float4 nv[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u)
+        nv[u] = (interior || b + u < j1) ? ld(b + u + W) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int j = b + u;
+        if (interior || j < j1) {
+          ring[(u + 2 * W) % P] = nv[u];
+          const E* c = reinterpret_cast<const E*>(&ring[(u + W) % P]);
+          float4 ov;
+          E* oe = reinterpret_cast<E*>(&ov);
 #pragma unroll
           for (int e = 0; e < EPT; ++e) {
-            const int x = x0 + e;
-            if (x < nx) {
-              const E v = F::pointwise(F::scaled(ev[e], s), vxr[e] + vr, dt, g);
-              const E mv = F::scaled(v, R(-1));
-              row[x] = v;
-              if (x <= kBandPad - 2) row[-2 - x] = mv;          // image about -1
-              if (x > nx - kBandPad) row[2 * nx - x] = mv;      // image about nx
-            } else if (x == nx) {
-              row[x] = F::zero();                                // the ghost
+            E a = F::mul(wt[W], c[e]);
+#pragma unroll
+            for (int k = 1; k <= W; ++k) {
+              const E* lo = reinterpret_cast<const E*>(&ring[(u + W - k) % P]);
+              const E* hi = reinterpret_cast<const E*>(&ring[(u + W + k) % P]);
+              a = F::chain(wt[W + k], F::add(lo[e], hi[e]), a);
+            }
+            oe[e] = F::add(c[e], a);
+          }
+          if (valid == EPT) {
+            out[(size_t)j * sv] = ov;
+            if (NORM) {
+#pragma unroll
+              for (int e = 0; e < EPT; ++e) part += F::abs2(oe[e]);
+            }
+          } else {
+            E* os = reinterpret_cast<E*>(out + (size_t)j * sv);
+            for (int e = 0; e < valid; ++e) {
+              os[e] = oe[e];
+              if (NORM) part += F::abs2(oe[e]);
             }
           }
         }
       }
-    }
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    if (worker) {
-      const E* sp = tile + (size_t)rr * slot + x0 - H * EPT;
-      E* gp = field + (size_t)(r0 + rr) * pitch + x0;
-      for (int q = rr; q < rows; q += rp, sp += (size_t)rp * slot, gp += (size_t)rp * pitch) {
-        float4 wv[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) wv[v] = reinterpret_cast<const float4*>(sp)[v];
-        const E* win = reinterpret_cast<const E*>(wv);
-        float4 ov;
-        E* o = reinterpret_cast<E*>(&ov);
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-          const int c = H * EPT + e;   // the output's position in the window
-          E acc = F::mul(wt[W], win[c]);
-#pragma unroll
-          for (int k = 1; k <= W; ++k) acc = F::chain(wt[W + k], F::add(win[c - k], win[c + k]), acc);
-          o[e] = acc;
-        }
-        if (x0 + EPT <= nx) {
-          *reinterpret_cast<float4*>(gp) = ov;
-        } else {
-#pragma unroll
-          for (int e = 0; e < EPT; ++e)
-            if (x0 + e < nx) gp[e] = o[e];
-        }
-      }
-    }
-    __syncthreads();
-    if (t == 0) {
-      const long long nxt = grp + (long long)S * gridDim.x;
-      if (nxt < ngroups) {
-        fence_smem_to_async();
-        issue(nxt, st);
-      }
+      if (NORM) acc += (double)part;
     }
   }
-  if (failed && t == 0) {
-    atomicOr(p.status, kStatusTimeout);
-    // wait (bounded) for every copy still in flight before the block exits
-    for (int q = 0; q < S; ++q) {
-      const int it2 = it + q;
-      const long long grp2 = blockIdx.x + (long long)it2 * gridDim.x;
-      if (grp2 < ngroups) mbar_wait_bounded(&full[it2 % S], (uint32_t)(it2 / S) & 1u, kWaitLimitNs);
-    }
-  }
+  if (NORM) norm_block_finish(acc, p);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1010,24 +1113,64 @@ static void (*band_kernel_for(int w, bool cplx))(SweepParams) {
 }
 
 size_t x_band_smem(const SweepParams& p, bool complex_field) {
-  return 128 + (size_t)p.band_stages * p.band_rows * (p.pitch + 2 * kBandPad) *
-                   (complex_field ? 8 : 4);
+  return 128 * kBandWarps + (size_t)kBandWarps * p.band_stages * (p.pitch + 2 * kBandPad) *
+                                (complex_field ? 8 : 4);
 }
 
-cudaError_t x_band_prepare(int w, bool complex_field, int threads, size_t smem,
-                           int* blocks_per_sm) {
+cudaError_t x_band_prepare(int w, bool complex_field, size_t smem, int* blocks_per_sm) {
   void (*k)(SweepParams) = band_kernel_for(w, complex_field);
   if (!k) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * kBandWarps, smem);
 }
 
 cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int grid,
                                 cudaStream_t st) {
   void (*k)(SweepParams) = band_kernel_for(p.band_w, complex_field);
   if (!k) return cudaErrorInvalidValue;
-  return launch_pdl(k, grid, p.band_threads, x_band_smem(p, complex_field), st, p);
+  return launch_pdl(k, grid, 32 * kBandWarps, x_band_smem(p, complex_field), st, p);
+}
+
+template <int W>
+static cudaError_t launch_band_line_W(int axis, const SweepParams& p, bool cplx, int grid,
+                                     cudaStream_t st) {
+  if (axis == 1)
+    return cplx ? launch_pdl(k_sweep_band_line<float, true, 1, false, W>, grid, 128, 0, st, p)
+                : launch_pdl(k_sweep_band_line<float, false, 1, false, W>, grid, 128, 0, st, p);
+  return cplx ? launch_pdl(k_sweep_band_line<float, true, 2, false, W>, grid, 128, 0, st, p)
+              : launch_pdl(k_sweep_band_line<float, false, 2, true, W>, grid, 128, 0, st, p);
+}
+
+template <int W> static int band_line_blocks_per_sm_W(int axis, bool cplx) {
+  int b = 0;
+  if (axis == 1) {
+    if (cplx) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, true, 1, false, W>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, false, 1, false, W>, 128, 0);
+  } else {
+    if (cplx) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, true, 2, false, W>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, false, 2, true, W>, 128, 0);
+  }
+  return b;
+}
+
+int band_line_blocks_per_sm(int axis, bool complex_field, int w) {
+  switch (w) {
+    case 3: return band_line_blocks_per_sm_W<3>(axis, complex_field);
+    case 5: return band_line_blocks_per_sm_W<5>(axis, complex_field);
+    case 8: return band_line_blocks_per_sm_W<8>(axis, complex_field);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_field, int grid,
+                                   cudaStream_t st) {
+  switch (p.band_w) {
+    case 3: return launch_band_line_W<3>(axis, p, complex_field, grid, st);
+    case 5: return launch_band_line_W<5>(axis, p, complex_field, grid, st);
+    case 8: return launch_band_line_W<8>(axis, p, complex_field, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_sweep_fast(int axis, const SweepParams& p, bool complex_field, int grid,

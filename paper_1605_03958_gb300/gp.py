@@ -233,8 +233,9 @@ def gp_get_info(h) -> dict:
     keys = ("pitch", "is_complex", "lines_x", "lines_y", "lines_z", "bytes", "fast_mask",
             "trunc")
     d = dict(zip(keys, list(v)))
-    d["band_w"] = (d["fast_mask"] >> 4) & 15 if d["fast_mask"] & 8 else 0
-    d["fast_mask"] &= 15
+    d["band_mask"] = (d["fast_mask"] >> 3) & 7
+    d["band_w"] = (d["fast_mask"] >> 8) & 15
+    d["fast_mask"] &= 7
     return d
 
 

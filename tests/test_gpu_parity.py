@@ -344,17 +344,20 @@ def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mod
         s.close()
     monkeypatch.delenv("GP_SWEEP_KERNELS", raising=False)
     assert outs["tile"][1]["fast_mask"] == 0
-    assert outs["stream"][1]["band_w"] == 0
+    assert outs["stream"][1]["band_mask"] == 0
     if shape[0] >= 16:
-        assert (outs["auto"][1]["fast_mask"] & 7) == 7, outs["auto"][1]
-        assert (outs["stream"][1]["fast_mask"] & 7) == 7, outs["stream"][1]
-    # h = 0.2, dt = 0.004: a = 0.025 (imaginary) and 0.025 i both need half-width 5;
-    # rows shorter than 8 points keep the streaming x kernel
-    assert outs["auto"][1]["band_w"] == (0 if shape[0] < 8 else 5), outs["auto"][1]
+        assert outs["auto"][1]["fast_mask"] == 7, outs["auto"][1]
+        assert outs["stream"][1]["fast_mask"] == 7, outs["stream"][1]
+    # lines shorter than 8 points keep the streaming kernels; h = 0.2, 0.18, 0.22 and
+    # dt = 0.004 give a = 0.025, 0.031, 0.021 (times i in real time): half-width 5
+    want = (1 if shape[0] >= 8 else 0) | 2 | 4
+    assert outs["auto"][1]["band_mask"] == want, outs["auto"][1]
+    assert outs["auto"][1]["band_w"] == 5, outs["auto"][1]
     # FP32 rounding, amplified by the nonlinear phase (dt g |psi|^2 ~ 0.25 per step at
     # g = 3000) over 20 steps: measured up to 3.1e-6 of max|psi| at g = 3000
     tol = (3e-6 if g < 1000 else 1e-5) * np.max(np.abs(ref))
     for kind in outs:
         assert np.max(np.abs(outs[kind][0] - ref)) <= tol, kind
-    assert np.max(np.abs(outs["auto"][0] - outs["tile"][0])) <= tol
-    assert np.max(np.abs(outs["stream"][0] - outs["tile"][0])) <= tol
+    # each path within tol of the oracle, so any two within 2 tol of each other
+    assert np.max(np.abs(outs["auto"][0] - outs["tile"][0])) <= 2 * tol
+    assert np.max(np.abs(outs["stream"][0] - outs["tile"][0])) <= 2 * tol
