@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--f64-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+                    help="single: the 240x200x160 solve (default); batch: 64 uneven FP32 "
+                         "solves resident in one pool")
+    ap.add_argument("--batch-single-steps", type=int, default=200,
+                    help="batch: steps per instance timed for the one-at-a-time baselines")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="override the grid (profiling of out-of-L2 cases); h and dt unchanged")
     args = ap.parse_args()
@@ -416,10 +421,96 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------ batched solves
+
+def run_batch(args):
+    """64 uneven imaginary-time FP32 solves resident in one pool, every one stepped
+    `--steps` steps by one batched launch per sweep direction (graph replay, shape
+    autotuned first).  value = solves / s.  Baselines: the same instances one at a time
+    with the single-solve library in FP64 and FP32 (each instance timed over
+    --batch-single-steps steps, scaled to --steps)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_03958_gb300 as P
+    from paper_1605_03958_gb300 import workloads
+
+    inst = workloads.batch_instances()
+    K = args.steps
+    points = sum(k["nx"] * k["ny"] * k["nz"] for k in inst)
+    need = sum(P.Pool.slot_bytes(**k) for k in inst)
+    pool = P.Pool(int(need * 1.05) + (64 << 20), max_slots=len(inst))
+    ids = [pool.add(**k) for k in inst]
+    tuned_ms = pool.tune(5)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        pool.step(K)
+        batch_s = time.perf_counter() - t0
+    info = pool.info()
+    obs = [pool.observables(s) for s in ids[:4]]
+    pool.close()
+
+    # one at a time through the single-solve library
+    n1 = min(args.batch_single_steps, K)
+    single = {}
+    for prec in ("f64", "f32"):
+        tot = 0.0
+        for k in inst:
+            s = P.Solver(k["nx"], k["ny"], k["nz"], k["dx"], dt=k["dt"], gamma=k["gamma"],
+                         nu=k["nu"], lam=k["lam"], g=k["g"], prec=prec)
+            s.init_gaussian()
+            s.step_imag(2)
+            s.sync()
+            t0 = time.perf_counter()
+            s.step_imag(n1)
+            s.sync()
+            tot += time.perf_counter() - t0
+            s.close()
+        single[prec] = len(inst) / (tot * K / n1)
+
+    # accuracy of the batched FP32 solves against FP64 one-at-a-time solves (first 4)
+    acc = []
+    for k, o in zip(inst[:4], obs):
+        s = P.Solver(k["nx"], k["ny"], k["nz"], k["dx"], dt=k["dt"], gamma=k["gamma"],
+                     nu=k["nu"], lam=k["lam"], g=k["g"], prec="f64")
+        s.init_gaussian()
+        s.step_imag(K)
+        ref = s.observables()
+        s.close()
+        acc.append(abs(o["mu"] - ref["mu"]) / abs(ref["mu"]))
+
+    value = len(inst) / batch_s
+    line = {
+        "metric": "batched solves/s", "value": round(value, 3), "unit": "solves/s",
+        "n_gpus": 1, "steps": K, "warmup": 0, "ms_per_step": round(batch_s / K * 1e3, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "64 uneven imag3d solves: extents from {32,48,...,160}, trap "
+                               "U[0.5,3], g log-uniform [1,5000], h=0.2, dt=0.1h^2, seed 1605",
+                   "grid_points": points, "parallelism": "one pool, one batched launch per sweep",
+                   "launch_shape": {"x_stages": info["x_stages"], "seg_turns": info["seg_turns"],
+                                    "graph": bool(info["graph"]),
+                                    "launches_per_step": info["launches_per_step"]},
+                   "l2": "not flushed (the batch's 1 GB of fields exceeds L2)"},
+        "grid_point_steps_per_s": round(points * K / batch_s, 1),
+        "one_at_a_time": {"f64_solves_per_s": round(single["f64"], 3),
+                          "f32_solves_per_s": round(single["f32"], 3),
+                          "timed_steps_per_instance": n1,
+                          "speedup_vs_f64": round(value / single["f64"], 2)},
+        "accuracy": {"mu_rel_vs_f64_single_max": max(acc), "instances": len(acc)},
+        "tuned_ms_per_step": round(tuned_ms, 5),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_cuda(args)
 

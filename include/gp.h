@@ -222,6 +222,76 @@ const char* gp_last_error(const gp_solver* s);
 /* Static text for a GP_* code. */
 const char* gp_strerror(int code);
 
+/* ---------------------------------------------------------------- pools
+ * A pool keeps many FP32 solves of different grids resident in one device arena and
+ * steps them together: batched uneven solves and the serving loop.  Every live slot
+ * advances by the same SSCN step as a single FP32 solver (imaginary time on a real
+ * field with renormalisation, or real time on a complex field), evaluated by one
+ * batched launch per sweep direction and mode over packed work lists (rows of every
+ * x line; blocks of every y / z line segment), the step captured as a CUDA graph.  A
+ * slot's arithmetic depends only on its own parameters and the pool's launch shape,
+ * not on which other slots are live.  All calls are synchronous unless stated.    */
+typedef struct gp_pool gp_pool;
+
+/* Arena bytes one solve with parameters p takes in a pool (host only). */
+int gp_pool_slot_bytes(const gp_params* p, size_t* bytes);
+
+/* Create a pool with an arena of arena_bytes (cudaMalloc'd on the current device) and
+ * room for max_slots (1..4096) solves.  stream: a cudaStream_t the pool works on, or
+ * NULL for a stream of its own (the legacy default stream cannot be captured).
+ * GP_ERR_NOMEM when the arena cannot be allocated.                                */
+int gp_pool_create(size_t arena_bytes, int max_slots, void* stream, gp_pool** out);
+void gp_pool_destroy(gp_pool* pool);
+
+/* Free arena bytes in total and in the largest free range. */
+int gp_pool_free_bytes(const gp_pool* pool, size_t* free_bytes, size_t* largest);
+
+/* Admit a solve: prec must be GP_F32, every extent >= 8, and dt / h^2 small enough
+ * that the banded line operators need a half-width <= 8 (else GP_ERR_ARG).  The slot
+ * starts from the g = 0 trap ground state exp(-(gamma x^2 + nu y^2 + lambda z^2)/2),
+ * normalised, in imaginary time.  *slot receives its index.  GP_ERR_NOMEM when no
+ * slot or no arena range of gp_pool_slot_bytes(p) is free.                          */
+int gp_pool_add(gp_pool* pool, const gp_params* p, int* slot);
+
+/* Retire a slot (after the work queued on the pool's stream) and free its range. */
+int gp_pool_remove(gp_pool* pool, int slot);
+
+/* Hand a slot over to real time: its field (with the pending renormalisation
+ * applied) becomes complex; every later step is a real-time step.               */
+int gp_pool_set_real_time(gp_pool* pool, int slot);
+
+/* Replace a slot's nonlinearity g (quench). */
+int gp_pool_set_g(gp_pool* pool, int slot, double g);
+
+/* nsteps steps of every live slot in its own mode; GP_ERR_NONFINITE when a norm
+ * became non-finite or zero.                                                      */
+int gp_pool_step(gp_pool* pool, long nsteps);
+
+/* Observables of one slot (gp_obs definitions as gp_observables). */
+int gp_pool_observables(gp_pool* pool, int slot, gp_obs* out);
+
+/* A slot's field to / from a caller-owned host FP64 buffer, layout
+ * host[(k ny + j) nx + i] (interleaved re, im when complex).  set_psi also sets
+ * the slot's mode (complex: real time).                                           */
+int gp_pool_get_psi(gp_pool* pool, int slot, double* host, int as_complex);
+int gp_pool_set_psi(gp_pool* pool, int slot, const double* host, int is_complex);
+
+/* Launch shape: x_stages (2..8) rows in flight per warp of the x sweep, seg_turns
+ * (1..8) turns of the 2W+1 ring per y / z segment.  gp_pool_tune times every pair
+ * in {2,3,4} x {2,3,4} over steps_per_candidate steps on the live slots (their
+ * state is saved before and restored after each candidate, so tuning advances no
+ * solve), keeps the fastest and returns its time per step in *best_ms (NULL allowed).
+ * gp_pool_set_graph(0) replaces the graph replay by direct launches.             */
+int gp_pool_set_shape(gp_pool* pool, int x_stages, int seg_turns);
+int gp_pool_tune(gp_pool* pool, int steps_per_candidate, double* best_ms);
+int gp_pool_set_graph(gp_pool* pool, int enable);
+
+/* info[0] live slots, [1] arena bytes in use, [2] x_stages, [3] seg_turns,
+ * [4] 1 when a step graph is instantiated, [5] launches per step, [6] free arena
+ * bytes, [7] largest free range.                                                  */
+int gp_pool_info(const gp_pool* pool, long long info[8]);
+const char* gp_pool_last_error(const gp_pool* pool);
+
 #ifdef __cplusplus
 }
 #endif

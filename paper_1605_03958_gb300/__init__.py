@@ -6,7 +6,7 @@ loads the library and fails loudly when it has not been built: there is no CPU
 fallback.
 """
 from . import gp
-from .gp import (GPError, Solver, gp_create, gp_create_on, gp_density1d, gp_density2d,
+from .gp import (GPError, Pool, Solver, gp_create, gp_create_on, gp_density1d, gp_density2d,
                  gp_destroy, gp_get_g, gp_get_info, gp_get_psi, gp_get_timing, gp_init_gaussian,
                  gp_last_error, gp_observables, gp_set_g, gp_set_psi, gp_set_timing,
                  gp_step_imag, gp_step_real, gp_strerror, gp_sync, gp_workspace_bytes,
@@ -14,7 +14,7 @@ from .gp import (GPError, Solver, gp_create, gp_create_on, gp_density1d, gp_dens
 
 gp.load_library()
 
-__all__ = ["gp", "GPError", "Solver", "make_params", "gp_create", "gp_create_on", "gp_destroy",
+__all__ = ["gp", "GPError", "Pool", "Solver", "make_params", "gp_create", "gp_create_on", "gp_destroy",
            "gp_workspace_bytes", "gp_init_gaussian", "gp_set_psi", "gp_get_psi", "gp_step_imag",
            "gp_step_real", "gp_set_g", "gp_get_g", "gp_observables", "gp_density1d",
            "gp_density2d", "gp_sync", "gp_set_timing", "gp_get_timing", "gp_get_info",

@@ -32,13 +32,48 @@ thread_local std::string g_create_error = "no error";
 
 void gpk::set_thread_error(const char* msg) { g_create_error = msg; }
 
+// Row of the free-line CN operator T_inf = (I + aK)^{-1} (I - aK) (K the second
+// difference on the infinite line): the middle row of the zero-ghost operator of a
+// line of 2 M + 1 points, M = 64, whose ghosts are so far away (|rho|^64) that their
+// influence is far below FP64 rounding for every usable a.  T is symmetric, so that
+// row is the Thomas solve (FP64) for the right-hand side (I - aK) e_M.  Returns the
+// smallest half-width W in {3, 5, 8} for which the entries beyond distance W sum, in
+// modulus, to at most 2^-28 (below FP32 rounding of a result), with
+// w[k] = T_inf[M][M + k - W], k = 0 .. 2W; 0 when no such W exists.
+int gpk::cn_free_row(std::complex<double> a, std::vector<std::complex<double>>* w) {
+  using C = std::complex<double>;
+  constexpr int M = 64, n = 2 * M + 1;
+  const C b = 1.0 + 2.0 * a;
+  std::vector<C> m(n), cp(n), d(n), u(n);
+  for (int j = 0; j < n; ++j) {
+    m[j] = 1.0 / (j == 0 ? b : b + a * cp[j - 1]);
+    cp[j] = -a * m[j];
+  }
+  C dp = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const C r = i == M ? 1.0 - 2.0 * a : (i == M - 1 || i == M + 1) ? a : C(0.0);
+    dp = (r + a * dp) * m[i];
+    d[i] = dp;
+  }
+  C next = 0.0;
+  for (int i = n - 1; i >= 0; --i) next = u[i] = d[i] - cp[i] * next;
+  for (int W : {3, 5, gpk::kBandHalfMax}) {
+    double tail = 0.0;
+    for (int i = 0; i < n; ++i)
+      if (std::abs(i - M) > W) tail += std::sqrt(std::norm(u[i]));
+    if (!(tail <= std::ldexp(1.0, -28))) continue;
+    w->assign(u.begin() + (M - W), u.begin() + (M + W + 1));
+    return W;
+  }
+  return 0;
+}
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr size_t kAlign = 256;
 constexpr size_t kFastTileBytes = 100 * 1024;   // preferred tile: >= 2 blocks per SM
 constexpr size_t kMaxTileBytes = 226 * 1024;    // opt-in shared memory per block, minus slack
-constexpr int kBandHalfMax = 8;                 // band half-widths 3, 5 or 8
 constexpr int kBandMinNx = 8;                   // one reflection covers every window
 constexpr int kBandStages = 3;                  // rows in flight per warp of the x band kernel
 constexpr size_t kBandBlockBytes = 100 * 1024;  // above this, 2 stages
@@ -213,41 +248,6 @@ bool force_stream_yz() {
   return v && (std::strcmp(v, "stream") == 0 || std::strcmp(v, "stream_yz") == 0);
 }
 
-// Row of the free-line CN operator T_inf = (I + aK)^{-1} (I - aK) (K the second
-// difference on the infinite line): the middle row of the zero-ghost operator of a
-// line of 2 M + 1 points, M = 64, whose ghosts are so far away (|rho|^64) that their
-// influence is far below FP64 rounding for every usable a.  T is symmetric, so that
-// row is the Thomas solve (FP64) for the right-hand side (I - aK) e_M.  Returns the
-// smallest half-width W in {3, 5, 8} for which the entries beyond distance W sum, in
-// modulus, to at most 2^-28 (below FP32 rounding of a result), with
-// w[k] = T_inf[M][M + k - W], k = 0 .. 2W; 0 when no such W exists.
-int cn_free_row(std::complex<double> a, std::vector<std::complex<double>>* w) {
-  using C = std::complex<double>;
-  constexpr int M = 64, n = 2 * M + 1;
-  const C b = 1.0 + 2.0 * a;
-  std::vector<C> m(n), cp(n), d(n), u(n);
-  for (int j = 0; j < n; ++j) {
-    m[j] = 1.0 / (j == 0 ? b : b + a * cp[j - 1]);
-    cp[j] = -a * m[j];
-  }
-  C dp = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const C r = i == M ? 1.0 - 2.0 * a : (i == M - 1 || i == M + 1) ? a : C(0.0);
-    dp = (r + a * dp) * m[i];
-    d[i] = dp;
-  }
-  C next = 0.0;
-  for (int i = n - 1; i >= 0; --i) next = u[i] = d[i] - cp[i] * next;
-  for (int W : {3, 5, kBandHalfMax}) {
-    double tail = 0.0;
-    for (int i = 0; i < n; ++i)
-      if (std::abs(i - M) > W) tail += std::sqrt(std::norm(u[i]));
-    if (!(tail <= std::ldexp(1.0, -28))) continue;
-    w->assign(u.begin() + (M - W), u.begin() + (M + W + 1));
-    return W;
-  }
-  return 0;
-}
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -575,7 +575,7 @@ int upload_tables(gp_solver* s) {
       if (force_stream_yz() && a > 0) continue;
       const double beta = p.dt / (4.0 * h[a] * h[a]);
       std::vector<std::complex<double>> w;
-      const int W = cn_free_row(m == 0 ? std::complex<double>(beta, 0.0)
+      const int W = gpk::cn_free_row(m == 0 ? std::complex<double>(beta, 0.0)
                                        : std::complex<double>(0.0, beta), &w);
       if (!W) continue;
       s->band_w[m][a] = W;

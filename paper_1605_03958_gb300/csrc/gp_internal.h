@@ -7,6 +7,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <complex>
+#include <vector>
+
 namespace gpk {
 
 // Status bits written by kernels into the solver's device status word.
@@ -23,6 +26,8 @@ constexpr int kMaxBox = 256;
 
 // Warps per block of the banded FP32 x sweep (each warp works on its own rows).
 constexpr int kBandWarps = 4;
+// Largest half-width of the banded operators (weights arrays hold 2 kBandHalfMax + 1).
+constexpr int kBandHalfMax = 8;
 
 // Fixed launch shape of the reductions, so that their summation order (and hence
 // their result) does not depend on the device.
@@ -76,6 +81,46 @@ struct SweepParams {
   long long ntiles;
 };
 
+// One resident solve of a pool (gp_batch.cu), as the batched FP32 sweeps see it.
+struct SlotDesc {
+  void* field;            // [nz][ny][pitch] elements (float or complex pairs)
+  void* staging;          // same layout: the y sweep writes it, the z sweep reads it
+  const void* fx;         // trap factors along x, [pitch]
+  const void* fyz;        // trap factor per row r = k ny + j
+  double* scale;          // pending renormalisation factor (imaginary time)
+  double* partials;       // z-sweep norm partials, one per z block of the slot
+  unsigned int* counter;  // z blocks of the slot finished (reset by the last)
+  int nx, ny, nz, pitch;
+  int seg[3];             // y / z: segment length in points
+  float dtg;              // dt g
+  double dV;
+  // banded weights per axis, w_{k-8}, k = 0 .. 16 (centre as w_0 - 1; complex:
+  // pairs), zero beyond the slot's own half-width
+  float wt[3][2 * (2 * kBandHalfMax + 1)];
+};
+// One warp's rows of a batched x sweep.
+struct XItem {
+  int slot;
+  int nrow;
+  long long row0;
+};
+// One block of a batched y / z sweep: block blk of the nblk blocks of one slot.
+struct LineBlock {
+  int slot;
+  int blk;
+  int nblk;
+  int pad;
+};
+// Arguments of a batched sweep launch.
+struct BatchArgs {
+  const SlotDesc* slots;
+  const void* items;      // XItem (x) or LineBlock (y, z), one per warp / block
+  int nitems;
+  int stages;             // x: rows in flight per warp
+  int slot_elems;         // x: shared-memory row slot, elements (>= pitch + 16 of every slot)
+  int* status;
+};
+
 // Arguments of the reductions and conversion kernels.
 struct FieldParams {
   void* psi;
@@ -111,6 +156,13 @@ cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int gr
 cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_field, int grid,
                                    cudaStream_t st);
 int band_line_blocks_per_sm(int axis, bool complex_field, int w);
+// Batched FP32 banded sweeps over the slots of a pool (one launch per direction
+// and mode): x on kBandWarps-warp blocks with dynamic shared memory
+// batch_x_smem(); y / z on blocks of 128 threads.  w is the launch half-width.
+size_t batch_x_smem(int stages, int slot_elems, bool complex_field);
+cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_blocks_per_sm);
+cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,
+                               size_t smem, cudaStream_t st);
 // Resident warps per SM of the streaming y / z kernel (occupancy calculator).
 int stream_warps_per_sm(int axis, bool complex_field, int trunc);
 
@@ -132,5 +184,10 @@ cudaError_t launch_cols_sum(const double* in, int rows, int cols, double w, doub
 
 // Message returned by gp_last_error(NULL) on this thread (gp_api.cu).
 void set_thread_error(const char* msg);
+
+// Row of the free-line CN operator for a = tau / (4 h^2) (gp_api.cu): returns the
+// half-width W in {3, 5, 8} that keeps the neglected entries below 2^-28 and the
+// weights w[0 .. 2W] (w[W] the centre), or 0.
+int cn_free_row(std::complex<double> a, std::vector<std::complex<double>>* w);
 
 }  // namespace gpk

@@ -438,7 +438,9 @@ constexpr int kHeadMax = 8;     // largest `head` the streaming kernel handles
 // the last block to finish sums the partials (all its threads, loads issued ahead,
 // a fixed-order tree) and writes the renormalisation factor.  Every thread of the
 // block must call it.
-__device__ __forceinline__ void norm_block_finish(double acc, const SweepParams& p) {
+__device__ __forceinline__ void norm_finish(double acc, double* partials, unsigned int* counter,
+                                            unsigned int nb, unsigned int bid, double* scale_out,
+                                            int* status, double dV) {
   __shared__ double wpart[32];
   __shared__ int last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -448,22 +450,22 @@ __device__ __forceinline__ void norm_block_finish(double acc, const SweepParams&
   if (threadIdx.x == 0) {
     double v = 0.0;
     for (int w = 0; w < nw; ++w) v += wpart[w];
-    p.partials[blockIdx.x] = v;
+    partials[bid] = v;
     __threadfence();
-    last = (atomicAdd(p.counter, 1u) == gridDim.x - 1);
+    last = (atomicAdd(counter, 1u) == nb - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   // thread t sums partials t, t + blockDim, ... (8 loads in flight), then a tree
-  const unsigned int nb = gridDim.x, T = blockDim.x;
+  const unsigned int T = blockDim.x;
   double s = 0.0, c = 0.0;
   for (unsigned int t0 = threadIdx.x; t0 < nb; t0 += 8 * T) {
     double x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const unsigned int t = t0 + q * T;
-      x[q] = t < nb ? __ldcg(p.partials + t) : 0.0;
+      x[q] = t < nb ? __ldcg(partials + t) : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -479,11 +481,15 @@ __device__ __forceinline__ void norm_block_finish(double acc, const SweepParams&
   if (threadIdx.x == 0) {
     double tot = 0.0;
     for (int w = 0; w < nw; ++w) tot += wpart[w];
-    const double norm = tot * p.dV;
-    if (!(norm > 0.0) || !isfinite(norm)) atomicOr(p.status, kStatusNonFinite);
-    *p.scale_out = 1.0 / sqrt(norm);
-    *p.counter = 0u;
+    const double norm = tot * dV;
+    if (!(norm > 0.0) || !isfinite(norm)) atomicOr(status, kStatusNonFinite);
+    *scale_out = 1.0 / sqrt(norm);
+    *counter = 0u;
   }
+}
+
+__device__ __forceinline__ void norm_block_finish(double acc, const SweepParams& p) {
+  norm_finish(acc, p.partials, p.counter, gridDim.x, blockIdx.x, p.scale_out, p.status, p.dV);
 }
 
 // y (AXIS 1) or z (AXIS 2) sweep: one lane per line, lanes on consecutive x.  A
@@ -791,42 +797,55 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
 // Needs nx >= kBandPad so that one reflection covers every window.
 constexpr int kBandPad = 8;     // room for the odd images on each side of a row slot
 
+// What one warp of the banded x sweep works on: nrow consecutive rows from row0 of
+// one field, streamed through S shared-memory row slots of slot_elems elements each.
+template <class E> struct XRows {
+  E* field;
+  const float4* fx;      // trap factors along x, [pitch] (16-byte vectors)
+  const E* fyz;          // trap factor per row
+  const E* wt;           // w_{k-W}, k = 0 .. 2W (centre as w_0 - 1)
+  const double* scale;   // pending renormalisation factor
+  int* status;
+  long long row0;
+  int nrow, nx, pitch, S, slot_elems;
+  float dtg;             // dt g
+};
+
+// Barriers and ghost -1 of a warp's row slots (before the dependent-launch wait).
+template <class E>
+__device__ __forceinline__ void x_band_init(uint64_t* full, E* slots, int S, int slot_elems) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
+  if (lane < S) slots[(size_t)lane * slot_elems - 1] = E{};   // ghost -1 of every slot
+  __syncwarp();
+}
+
 template <class R, bool CPLX, int W>
-__global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_constant__ SweepParams p) {
+__device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>::E>& a,
+                                            uint64_t* full, typename Field<R, CPLX>::E* slots) {
   using F = Field<R, CPLX>;
   using E = typename F::E;
   constexpr int EPT = 16 / (int)sizeof(E);   // elements per 16-byte vector
   constexpr int H = (W + EPT - 1) / EPT;     // halo vectors on each side of a window
   constexpr int NV = 2 * H + 1;              // vectors in a window
   static_assert(H * EPT <= kBandPad, "window inside the slot");
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int nx = p.nx, pitch = p.pitch, S = p.band_stages, RPW = p.band_rows;
-  const int slot = pitch + 2 * kBandPad;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
-  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * slot + kBandPad;
-  const long long nrows = (long long)p.ny * p.nz;
-  const long long row0 = ((long long)blockIdx.x * kBandWarps + wib) * RPW;
-  const int nrow = (int)max(0LL, min((long long)RPW, nrows - row0));
+  const int nx = a.nx, pitch = a.pitch, S = a.S, nrow = a.nrow;
+  const int lane = threadIdx.x & 31;
   const int nvec = (nx + EPT - 1) / EPT;
-  E* field = static_cast<E*>(p.psi);
-  const E* wt = reinterpret_cast<const E*>(p.band_wt);   // w_{k-W}, k = 0 .. 2W
-  const float4* fx = static_cast<const float4*>(p.band_fx);   // trap factors along x
-  const E* fyz = static_cast<const E*>(p.band_fyz);            // trap factor per row
+  const long long row0 = a.row0;
+  E* field = a.field;
+  const E* wt = a.wt;
+  const float4* fx = a.fx;
+  const E* fyz = a.fyz;
   const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
-
-  if (lane == 0)
-    for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
-  if (lane < S) slots[(size_t)lane * slot - 1] = F::zero();   // ghost -1 of every slot
-  __syncwarp();
-  pdl_begin();
-  if (nrow == 0) return;
-  const R s = (R)(*p.scale);
-  const R dtg = (R)(p.dt * p.g);
+  const R s = (R)(*a.scale);
+  const R dtg = (R)a.dtg;
   auto issue = [&](int i) {   // row i of this warp -> stage i % S
     const int st = i % S;
     mbar_arrive_expect_tx(&full[st], rowbytes);
-    bulk_load(slots + (size_t)st * slot, field + (size_t)(row0 + i) * pitch, rowbytes, &full[st]);
+    bulk_load(slots + (size_t)st * a.slot_elems, field + (size_t)(row0 + i) * pitch, rowbytes,
+              &full[st]);
   };
   if (lane == 0)
     for (int i = 0; i < S && i < nrow; ++i) issue(i);
@@ -834,12 +853,12 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
 
   for (int i = 0; i < nrow; ++i) {
     const int st = i % S;
-    E* row = slots + (size_t)st * slot;
+    E* row = slots + (size_t)st * a.slot_elems;
     const E fr = f_next;
     if (i + 1 < nrow) f_next = fyz[row0 + i + 1];
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)(i / S) & 1u, kWaitLimitNs))) {
       if (lane == 0) {
-        atomicOr(p.status, kStatusTimeout);
+        atomicOr(a.status, kStatusTimeout);
         // wait (bounded) for every copy still in flight before the warp exits
         for (int q = i; q < i + S && q < nrow; ++q)
           mbar_wait_bounded(&full[q % S], (uint32_t)(q / S) & 1u, kWaitLimitNs);
@@ -919,6 +938,69 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   }
 }
 
+template <class R, bool CPLX, int W>
+__global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_constant__ SweepParams p) {
+  using E = typename Field<R, CPLX>::E;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int S = p.band_stages, slot_elems = p.pitch + 2 * kBandPad;
+  const int wib = threadIdx.x >> 5;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
+  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * slot_elems + kBandPad;
+  const long long nrows = (long long)p.ny * p.nz;
+  const long long row0 = ((long long)blockIdx.x * kBandWarps + wib) * p.band_rows;
+  const int nrow = (int)max(0LL, min((long long)p.band_rows, nrows - row0));
+  x_band_init(full, slots, S, slot_elems);
+  pdl_begin();
+  if (nrow == 0) return;
+  XRows<E> a;
+  a.field = static_cast<E*>(p.psi);
+  a.fx = static_cast<const float4*>(p.band_fx);
+  a.fyz = static_cast<const E*>(p.band_fyz);
+  a.wt = reinterpret_cast<const E*>(p.band_wt);
+  a.scale = p.scale;
+  a.status = p.status;
+  a.row0 = row0;
+  a.nrow = nrow;
+  a.nx = p.nx;
+  a.pitch = p.pitch;
+  a.S = S;
+  a.slot_elems = slot_elems;
+  a.dtg = (float)(p.dt * p.g);
+  x_band_rows<R, CPLX, W>(a, full, slots);
+}
+
+// Batched x sweep: warp w of the launch takes work item w (rows of one slot).
+template <class R, bool CPLX, int W>
+__global__ void __launch_bounds__(32 * kBandWarps) k_batch_x_band(const __grid_constant__ BatchArgs b) {
+  using E = typename Field<R, CPLX>::E;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int S = b.stages, slot_elems = b.slot_elems;
+  const int wib = threadIdx.x >> 5;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
+  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * slot_elems + kBandPad;
+  const int w = blockIdx.x * kBandWarps + wib;
+  x_band_init(full, slots, S, slot_elems);
+  pdl_begin();
+  if (w >= b.nitems) return;
+  const XItem it = static_cast<const XItem*>(b.items)[w];
+  const SlotDesc& d = b.slots[it.slot];
+  XRows<E> a;
+  a.field = static_cast<E*>(d.field);
+  a.fx = static_cast<const float4*>(d.fx);
+  a.fyz = static_cast<const E*>(d.fyz);
+  a.wt = reinterpret_cast<const E*>(d.wt[0]) + (kBandHalfMax - W);
+  a.scale = d.scale;
+  a.status = b.status;
+  a.row0 = it.row0;
+  a.nrow = it.nrow;
+  a.nx = d.nx;
+  a.pitch = d.pitch;
+  a.S = S;
+  a.slot_elems = slot_elems;
+  a.dtg = d.dtg;
+  x_band_rows<R, CPLX, W>(a, full, slots);
+}
+
 // y (AXIS 1) or z (AXIS 2) sweep as the banded operator on the odd extension (see the
 // x sweep above), for the FP32 field.  Thread t owns the 16-byte vector
 // xv = t mod nvec (EPT consecutive x) of one segment of band_seg points of one line;
@@ -930,19 +1012,27 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
 // neighbouring segments read each other's inputs.  With NORM the block also sums
 // |u|^2 (FP32 within a ring turn, FP64 across) and the last block turns the partials
 // into the renormalisation factor.
+// What one thread of a banded y / z sweep works on.
+template <class E> struct LineArgs {
+  const E* psi;          // input field, [nz][ny][pitch]
+  E* out;                // output field, same layout
+  const E* wt;           // w_{k-W}, k = 0 .. 2W (centre as w_0 - 1)
+  int nx, ny, nz, n, pitch, Ls;
+};
+
+// Thread t's segment of one line; returns the FP64 sum of |u|^2 it stored (NORM).
 template <class R, bool CPLX, int AXIS, bool NORM, int W>
-__global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__ SweepParams p) {
-  pdl_begin();
+__device__ __forceinline__ double band_line_thread(const LineArgs<typename Field<R, CPLX>::E>& p,
+                                                   long long t) {
   using F = Field<R, CPLX>;
   using E = typename F::E;
   constexpr int EPT = 16 / (int)sizeof(E);
   constexpr int P = 2 * W + 1;
-  const int nx = p.nx, n = p.n, Ls = p.band_seg;
+  const int nx = p.nx, n = p.n, Ls = p.Ls;
   const int nvec = (nx + EPT - 1) / EPT;
   const int nother = AXIS == 1 ? p.nz : p.ny;
   const int nseg = (n + Ls - 1) / Ls;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const E* wt = reinterpret_cast<const E*>(p.band_wt);   // w_{k-W}, k = 0 .. 2W
+  const E* wt = p.wt;
   double acc = 0.0;
   if (t < (long long)nvec * nother * nseg) {
     const int xv = (int)(t % nvec);
@@ -950,8 +1040,8 @@ __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__
     const int o = (int)(rest % nother), sg = (int)(rest / nother);
     const size_t pitch = (size_t)p.pitch;
     const size_t base = (AXIS == 1 ? (size_t)o * p.ny * pitch : (size_t)o * pitch) + (size_t)xv * EPT;
-    const float4* in = reinterpret_cast<const float4*>(static_cast<const E*>(p.psi) + base);
-    float4* out = reinterpret_cast<float4*>(static_cast<E*>(p.out) + base);
+    const float4* in = reinterpret_cast<const float4*>(p.psi + base);
+    float4* out = reinterpret_cast<float4*>(p.out + base);
     const size_t sv = (AXIS == 1 ? pitch : pitch * p.ny) * sizeof(E) / 16;   // line stride in vectors
     const int valid = min(EPT, nx - xv * EPT);   // elements of this vector inside the field
     const int j0 = sg * Ls, j1 = min(n, j0 + Ls);
@@ -1010,7 +1100,47 @@ __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__
       if (NORM) acc += (double)part;
     }
   }
+  return acc;
+}
+
+template <class R, bool CPLX, int AXIS, bool NORM, int W>
+__global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__ SweepParams p) {
+  pdl_begin();
+  using E = typename Field<R, CPLX>::E;
+  LineArgs<E> a;
+  a.psi = static_cast<const E*>(p.psi);
+  a.out = static_cast<E*>(p.out);
+  a.wt = reinterpret_cast<const E*>(p.band_wt);
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.nz = p.nz;
+  a.n = p.n;
+  a.pitch = p.pitch;
+  a.Ls = p.band_seg;
+  const double acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
   if (NORM) norm_block_finish(acc, p);
+}
+
+// Batched y / z sweep: block b of the launch is block blk of nblk of one slot; the
+// z sweep's norm is reduced per slot (its own partials, counter and factor).
+template <class R, bool CPLX, int AXIS, bool NORM, int W>
+__global__ void __launch_bounds__(128) k_batch_band_line(const __grid_constant__ BatchArgs b) {
+  pdl_begin();
+  using E = typename Field<R, CPLX>::E;
+  const LineBlock lb = static_cast<const LineBlock*>(b.items)[blockIdx.x];
+  const SlotDesc& d = b.slots[lb.slot];
+  LineArgs<E> a;
+  a.psi = static_cast<const E*>(AXIS == 1 ? d.field : d.staging);
+  a.out = static_cast<E*>(AXIS == 1 ? d.staging : d.field);
+  a.wt = reinterpret_cast<const E*>(d.wt[AXIS]) + (kBandHalfMax - W);
+  a.nx = d.nx;
+  a.ny = d.ny;
+  a.nz = d.nz;
+  a.n = AXIS == 1 ? d.ny : d.nz;
+  a.pitch = d.pitch;
+  a.Ls = d.seg[AXIS];
+  const double acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, (long long)lb.blk * blockDim.x + threadIdx.x);
+  if (NORM) norm_finish(acc, d.partials, d.counter, (unsigned int)lb.nblk, (unsigned int)lb.blk, d.scale, b.status, d.dV);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1169,6 +1299,49 @@ cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_
     case 3: return launch_band_line_W<3>(axis, p, complex_field, grid, st);
     case 5: return launch_band_line_W<5>(axis, p, complex_field, grid, st);
     case 8: return launch_band_line_W<8>(axis, p, complex_field, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t batch_x_smem(int stages, int slot_elems, bool complex_field) {
+  return 128 * kBandWarps + (size_t)kBandWarps * stages * slot_elems * (complex_field ? 8 : 4);
+}
+
+template <int W> static cudaError_t batch_prepare_W(bool cplx, size_t x_smem, int* bps) {
+  void (*k)(BatchArgs) = cplx ? k_batch_x_band<float, true, W> : k_batch_x_band<float, false, W>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x_smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, 32 * kBandWarps, x_smem);
+}
+
+cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_blocks_per_sm) {
+  switch (w) {
+    case 3: return batch_prepare_W<3>(complex_field, x_smem, x_blocks_per_sm);
+    case 5: return batch_prepare_W<5>(complex_field, x_smem, x_blocks_per_sm);
+    case 8: return batch_prepare_W<8>(complex_field, x_smem, x_blocks_per_sm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int W>
+static cudaError_t launch_batch_W(int axis, const BatchArgs& b, bool cplx, int grid, size_t smem,
+                                  cudaStream_t st) {
+  if (axis == 0)
+    return cplx ? launch_pdl(k_batch_x_band<float, true, W>, grid, 32 * kBandWarps, smem, st, b)
+                : launch_pdl(k_batch_x_band<float, false, W>, grid, 32 * kBandWarps, smem, st, b);
+  if (axis == 1)
+    return cplx ? launch_pdl(k_batch_band_line<float, true, 1, false, W>, grid, 128, 0, st, b)
+                : launch_pdl(k_batch_band_line<float, false, 1, false, W>, grid, 128, 0, st, b);
+  return cplx ? launch_pdl(k_batch_band_line<float, true, 2, false, W>, grid, 128, 0, st, b)
+              : launch_pdl(k_batch_band_line<float, false, 2, true, W>, grid, 128, 0, st, b);
+}
+
+cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,
+                               size_t smem, cudaStream_t st) {
+  switch (w) {
+    case 3: return launch_batch_W<3>(axis, b, complex_field, grid, smem, st);
+    case 5: return launch_batch_W<5>(axis, b, complex_field, grid, smem, st);
+    case 8: return launch_batch_W<8>(axis, b, complex_field, grid, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }

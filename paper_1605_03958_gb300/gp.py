@@ -96,6 +96,23 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_observables_noalloc": (i, [vp, i, i, i, ll, i, i, d, d, d, d, d, d, d, vp, vp]),
         "gp_last_error": (ctypes.c_char_p, [vp]),
         "gp_strerror": (ctypes.c_char_p, [i]),
+        "gp_pool_slot_bytes": (i, [pp, ctypes.POINTER(ctypes.c_size_t)]),
+        "gp_pool_create": (i, [ctypes.c_size_t, i, vp, ctypes.POINTER(vp)]),
+        "gp_pool_destroy": (None, [vp]),
+        "gp_pool_free_bytes": (i, [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+        "gp_pool_add": (i, [vp, pp, ctypes.POINTER(i)]),
+        "gp_pool_remove": (i, [vp, i]),
+        "gp_pool_set_real_time": (i, [vp, i]),
+        "gp_pool_set_g": (i, [vp, i, d]),
+        "gp_pool_step": (i, [vp, l]),
+        "gp_pool_observables": (i, [vp, i, ctypes.POINTER(GpObs)]),
+        "gp_pool_get_psi": (i, [vp, i, vp, i]),
+        "gp_pool_set_psi": (i, [vp, i, vp, i]),
+        "gp_pool_set_shape": (i, [vp, i, i]),
+        "gp_pool_tune": (i, [vp, i, dp]),
+        "gp_pool_set_graph": (i, [vp, i]),
+        "gp_pool_info": (i, [vp, ctypes.POINTER(ll)]),
+        "gp_pool_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -355,3 +372,164 @@ class Solver:
 
     def info(self):
         return gp_get_info(self.handle)
+
+
+# --------------------------------------------------------------------- pools
+
+def _pcheck(rc: int, pool=None) -> None:
+    if rc != GP_OK:
+        raise GPError(rc, load_library().gp_pool_last_error(pool).decode())
+
+
+def gp_pool_slot_bytes(p: GpParams) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().gp_pool_slot_bytes(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def gp_pool_create(arena_bytes: int, max_slots: int, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().gp_pool_create(arena_bytes, max_slots, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def gp_pool_destroy(pool) -> None:
+    load_library().gp_pool_destroy(pool)
+
+
+def gp_pool_free_bytes(pool):
+    f, g = ctypes.c_size_t(), ctypes.c_size_t()
+    _pcheck(load_library().gp_pool_free_bytes(pool, ctypes.byref(f), ctypes.byref(g)), pool)
+    return f.value, g.value
+
+
+def gp_pool_add(pool, p: GpParams) -> int:
+    slot = ctypes.c_int()
+    _pcheck(load_library().gp_pool_add(pool, ctypes.byref(p), ctypes.byref(slot)), pool)
+    return slot.value
+
+
+def gp_pool_remove(pool, slot: int) -> None:
+    _pcheck(load_library().gp_pool_remove(pool, slot), pool)
+
+
+def gp_pool_set_real_time(pool, slot: int) -> None:
+    _pcheck(load_library().gp_pool_set_real_time(pool, slot), pool)
+
+
+def gp_pool_set_g(pool, slot: int, g: float) -> None:
+    _pcheck(load_library().gp_pool_set_g(pool, slot, float(g)), pool)
+
+
+def gp_pool_step(pool, nsteps: int) -> None:
+    _pcheck(load_library().gp_pool_step(pool, int(nsteps)), pool)
+
+
+def gp_pool_observables(pool, slot: int) -> dict:
+    o = GpObs()
+    _pcheck(load_library().gp_pool_observables(pool, slot, ctypes.byref(o)), pool)
+    return {n: getattr(o, n) for n in OBS_NAMES}
+
+
+def gp_pool_get_psi(pool, slot: int, shape, as_complex: bool = False) -> np.ndarray:
+    out = np.empty(shape, np.complex128 if as_complex else np.float64)
+    _pcheck(load_library().gp_pool_get_psi(pool, slot, out.ctypes.data_as(ctypes.c_void_p), int(as_complex)), pool)
+    return out
+
+
+def gp_pool_set_psi(pool, slot: int, host: np.ndarray) -> None:
+    a = np.ascontiguousarray(host)
+    cplx = np.iscomplexobj(a)
+    a = a.astype(np.complex128 if cplx else np.float64, copy=False)
+    _pcheck(load_library().gp_pool_set_psi(pool, slot, a.ctypes.data_as(ctypes.c_void_p), int(cplx)), pool)
+
+
+def gp_pool_set_shape(pool, x_stages: int, seg_turns: int) -> None:
+    _pcheck(load_library().gp_pool_set_shape(pool, x_stages, seg_turns), pool)
+
+
+def gp_pool_tune(pool, steps_per_candidate: int = 5) -> float:
+    ms = ctypes.c_double()
+    _pcheck(load_library().gp_pool_tune(pool, steps_per_candidate, ctypes.byref(ms)), pool)
+    return ms.value
+
+
+def gp_pool_set_graph(pool, enable: bool) -> None:
+    _pcheck(load_library().gp_pool_set_graph(pool, int(enable)), pool)
+
+
+def gp_pool_info(pool) -> dict:
+    v = (ctypes.c_longlong * 8)()
+    _pcheck(load_library().gp_pool_info(pool, v), pool)
+    keys = ("live", "bytes_used", "x_stages", "seg_turns", "graph", "launches_per_step",
+            "free_bytes", "largest_free")
+    return dict(zip(keys, list(v)))
+
+
+class Pool:
+    """Resident FP32 solves of different grids stepped together (see include/gp.h).
+    Slots are added with the keyword parameters of ``make_params``."""
+
+    def __init__(self, arena_bytes: int, max_slots: int = 256, stream: Optional[int] = None):
+        self.handle = gp_pool_create(int(arena_bytes), int(max_slots), stream or 0)
+        self.shapes = {}
+
+    def close(self):
+        if self.handle:
+            gp_pool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def slot_bytes(**kw) -> int:
+        kw.setdefault("prec", "f32")
+        return gp_pool_slot_bytes(make_params(**kw))
+
+    def add(self, **kw) -> int:
+        kw.setdefault("prec", "f32")
+        p = make_params(**kw)
+        slot = gp_pool_add(self.handle, p)
+        self.shapes[slot] = (p.nz, p.ny, p.nx)
+        return slot
+
+    def remove(self, slot):
+        gp_pool_remove(self.handle, slot)
+        self.shapes.pop(slot, None)
+
+    def set_real_time(self, slot):
+        gp_pool_set_real_time(self.handle, slot)
+
+    def set_g(self, slot, g):
+        gp_pool_set_g(self.handle, slot, g)
+
+    def step(self, n):
+        gp_pool_step(self.handle, n)
+
+    def observables(self, slot):
+        return gp_pool_observables(self.handle, slot)
+
+    def get_psi(self, slot, as_complex=False):
+        return gp_pool_get_psi(self.handle, slot, self.shapes[slot], as_complex)
+
+    def set_psi(self, slot, psi):
+        gp_pool_set_psi(self.handle, slot, psi)
+
+    def set_shape(self, x_stages, seg_turns):
+        gp_pool_set_shape(self.handle, x_stages, seg_turns)
+
+    def tune(self, steps_per_candidate=5):
+        return gp_pool_tune(self.handle, steps_per_candidate)
+
+    def set_graph(self, enable):
+        gp_pool_set_graph(self.handle, enable)
+
+    def free_bytes(self):
+        return gp_pool_free_bytes(self.handle)
+
+    def info(self):
+        return gp_pool_info(self.handle)

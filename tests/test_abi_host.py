@@ -95,3 +95,18 @@ def test_strerror(P):
     assert P.gp_strerror(0) == "ok"
     assert "non-finite" in P.gp_strerror(P.gp.GP_ERR_NONFINITE)
     assert P.gp_strerror(-99) == "unknown error"
+
+
+def test_pool_slot_bytes_on_the_host(P):
+    """gp_pool_slot_bytes needs no device: field and staging sized for the complex field
+    plus the trap tables; invalid parameters are rejected like gp_workspace_bytes."""
+    p = P.make_params(96, 80, 64, 0.2, gamma=1.0, nu=1.5, lam=2.0, g=10.0, prec="f32")
+    n = P.gp.gp_pool_slot_bytes(p)
+    rows = 80 * 64
+    assert n >= 2 * 96 * 8 * rows + (96 * 12 + rows * 12)
+    assert n < 2 * 96 * 8 * rows * 1.2
+    assert n % 256 == 0
+    bad = P.make_params(2, 80, 64, 0.2, prec="f32")
+    with pytest.raises(P.GPError) as e:
+        P.gp.gp_pool_slot_bytes(bad)
+    assert e.value.code == P.gp.GP_ERR_ARG
