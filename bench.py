@@ -48,9 +48,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--f64-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single",
                     help="single: the 240x200x160 solve (default); batch: 64 uneven FP32 "
-                         "solves resident in one pool")
+                         "solves resident in one pool; serve: the continuous-batching server "
+                         "on a Poisson request stream")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-compare", type=int, default=100,
+                    help="serve: leading requests also served one at a time in FP64 and FP32")
     ap.add_argument("--batch-single-steps", type=int, default=200,
                     help="batch: steps per instance timed for the one-at-a-time baselines")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
@@ -505,12 +509,79 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------- serving
+
+def run_serve(args):
+    """The continuous-batching server on the seeded request stream (Poisson arrivals,
+    mean 200 / s; 70 % ground-state, 30 % quench requests), arrivals on the wall clock.
+    value = completed solves / s over the run; latency = finish - arrival.  The leading
+    --serve-compare requests are also served one at a time (FP64 and FP32 single
+    solvers, FIFO, same arrival times) and by the batched server alone."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_03958_gb300  # noqa: F401  (loads the library)
+    from paper_1605_03958_gb300 import workloads
+    from paper_1605_03958_gb300.serve import Server, serve_one_at_a_time
+
+    def summary(done):
+        lat = sorted(d["latency"] for d in done)
+        span = max(d["finished"] for d in done) - min(d["arrival"] for d in done)
+        return {"solves": len(done), "solves_per_s": round(len(done) / span, 3),
+                "p50_s": round(float(np.percentile(lat, 50)), 4),
+                "p99_s": round(float(np.percentile(lat, 99)), 4), "makespan_s": round(span, 3)}
+
+    import numpy as np
+    reqs = workloads.serve_requests(args.serve_requests)
+    srv = Server(quantum=100)
+    with ClockSampler(0) as clk:
+        done = srv.run(reqs, realtime=True)
+    full = summary(done)
+    stats = dict(srv.stats)
+    srv.close()
+
+    head = reqs[:args.serve_compare]
+    srv = Server(quantum=100)
+    b = srv.run(head, realtime=True)
+    srv.close()
+    f64 = serve_one_at_a_time(head, prec="f64", realtime=True)
+    f32 = serve_one_at_a_time(head, prec="f32", realtime=True)
+    by = {d["id"]: d for d in f64}
+    err = {"ground_mu_rel_max": 0.0, "quench_energy_rel_max": 0.0}
+    for d in b:
+        w = by[d["id"]]["obs"]
+        if d["kind"] == "ground":
+            err["ground_mu_rel_max"] = max(err["ground_mu_rel_max"], abs(d["obs"]["mu"] - w["mu"]) / abs(w["mu"]))
+        else:
+            err["quench_energy_rel_max"] = max(err["quench_energy_rel_max"],
+                                               abs(d["obs"]["energy"] - w["energy"]) / abs(w["energy"]))
+    line = {
+        "metric": "served solves/s", "value": full["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at 200/s (seed 3958): 70 % "
+                               "ground state (2000 imaginary steps), 30 % quench (500..5000 real "
+                               "steps from the g=0 Gaussian); extents multiples of 16 in "
+                               "[32,128]x[32,96]x[32,64], g log-uniform [1,1000], h=0.2, dt=0.1h^2",
+                   "quantum_steps": 100, "admission": "FIFO by free arena (half of free HBM)"},
+        "latency": {"p50_s": full["p50_s"], "p99_s": full["p99_s"]},
+        "run": full, "server": stats,
+        "compare_first_requests": {"requests": len(head), "batched": summary(b),
+                                   "one_at_a_time_f64": summary(f64), "one_at_a_time_f32": summary(f32),
+                                   "accuracy_vs_f64": err},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_cuda(args)
 
