@@ -77,6 +77,7 @@ constexpr size_t kMaxTileBytes = 226 * 1024;    // opt-in shared memory per bloc
 constexpr int kBandMinNx = 8;                   // one reflection covers every window
 constexpr int kBandStages = 3;                  // rows in flight per warp of the x band kernel
 constexpr size_t kBandBlockBytes = 100 * 1024;  // above this, 2 stages
+constexpr size_t kBandWarpBudget = 6 * 1024;   // x band: row slots of one warp for groups of rows
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -453,9 +454,16 @@ void fill_sweep_params(gp_solver* s) {
         q.band_w = s->band_w[m][0];
         const size_t slot_bytes = ((size_t)s->L.pitch[m] + 16) * rb * (m + 1);
         q.band_stages = gpk::kBandWarps * kBandStages * slot_bytes <= kBandBlockBytes ? kBandStages : 2;
+        // rows of 32 or more 16-byte vectors fill the lanes one at a time; shorter
+        // rows are taken in groups
+        const int ept = m == 0 ? 4 : 2;
+        q.band_group = (p.nx + ept - 1) / ept >= 32
+                           ? 1
+                           : gpk::x_band_group(p.nx, ept, q.band_stages, slot_bytes, kBandWarpBudget);
         const size_t smem = gpk::x_band_smem(q, m == 1);
         int bps = 0;
-        if (gpk::x_band_prepare(q.band_w, m == 1, smem, &bps) == cudaSuccess && bps > 0) {
+        if (gpk::x_band_prepare(q.band_w, m == 1, q.band_group > 1, smem, &bps) == cudaSuccess &&
+            bps > 0) {
           // rows per warp such that every warp is resident at once with equal work
           const long long rows = (long long)p.ny * p.nz;
           const long long cap = (long long)s->nsm * bps * gpk::kBandWarps;

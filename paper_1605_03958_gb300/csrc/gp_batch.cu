@@ -31,6 +31,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kMaxPoolSlots = 4096;
 constexpr size_t kMaxSmem = 227 * 1024;   // opt-in shared memory per block
+constexpr size_t kXWarpBudget = 6 * 1024;  // x: row slots of one warp for groups of rows
 constexpr int kWeights = 2 * gpk::kBandHalfMax + 1;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -179,6 +180,7 @@ struct gp_pool {
   int slot_elems[2] = {};      // x: shared-memory row slot per mode
   size_t x_smem[2] = {};
   int x_stages_used[2] = {2, 2};
+  int x_group_max[2] = {1, 1};
   int live_mode[2] = {};       // live slots per mode
   // launch shape (autotuned)
   int x_stages = 3, seg_turns = 3;
@@ -372,12 +374,25 @@ int rebuild(gp_pool* P) {
       for (int a = 0; a < 3; ++a) P->nitems[m][a] = 0;
       continue;
     }
-    // x: stages that fit shared memory, rows per warp such that every warp is
-    // resident at once
+    // x: stages that fit shared memory, rows per group per slot, rows per warp such
+    // that every warp is resident at once
     int st = P->x_stages;
-    while (st > 2 && gpk::batch_x_smem(st, P->slot_elems[m], cplx) > kMaxSmem) --st;
+    while (st > 2 && gpk::batch_x_smem(st, 1, P->slot_elems[m], cplx) > kMaxSmem) --st;
     P->x_stages_used[m] = st;
-    P->x_smem[m] = gpk::batch_x_smem(st, P->slot_elems[m], cplx);
+    const size_t slot_bytes = (size_t)P->slot_elems[m] * (cplx ? 8 : 4);
+    int gmax = 1;
+    std::vector<int> grp(ns, 1);
+    for (int i = 0; i < ns; ++i)
+      if (P->slots[i].live && P->slots[i].mode == m) {
+        grp[i] = gpk::x_band_group(P->slots[i].prm.nx, cplx ? 2 : 4, st, slot_bytes, kXWarpBudget);
+        gmax = std::max(gmax, grp[i]);
+      }
+    while (gmax > 1 && gpk::batch_x_smem(st, gmax, P->slot_elems[m], cplx) > kMaxSmem) {
+      --gmax;
+      for (int& g : grp) g = std::min(g, gmax);
+    }
+    P->x_group_max[m] = gmax;
+    P->x_smem[m] = gpk::batch_x_smem(st, gmax, P->slot_elems[m], cplx);
     int bps = 0;
     cudaError_t e = gpk::batch_prepare(P->wl[m][0], cplx, P->x_smem[m], &bps);
     if (e != cudaSuccess) return pcuda(P, e, "batch_prepare");
@@ -399,6 +414,8 @@ int rebuild(gp_pool* P) {
         it.slot = i;
         it.row0 = r;
         it.nrow = (int)std::min<long long>(rpw, rows - r);
+        it.group = grp[i];
+        it.pad = 0;
         xi.push_back(it);
       }
       const int ept = cplx ? 2 : 4;
@@ -445,6 +462,7 @@ int launch_step(gp_pool* P) {
       b.items = P->d_items[m][a];
       b.nitems = P->nitems[m][a];
       b.stages = P->x_stages_used[m];
+      b.group_max = P->x_group_max[m];
       b.slot_elems = P->slot_elems[m];
       b.status = P->d_status;
       const int grid = a == 0 ? (b.nitems + gpk::kBandWarps - 1) / gpk::kBandWarps : b.nitems;

@@ -64,7 +64,8 @@ struct SweepParams {
   float band_wt[2 * 17]; // free-line CN row w_{k - band_w}, k = 0 .. 2 band_w, centre as w_0 - 1 (complex: pairs)
   int band_w;            // half-width W of the band (3, 5 or 8)
   int band_rows;         // x: consecutive rows per warp
-  int band_stages;       // x: rows in flight per warp
+  int band_stages;       // x: groups of rows in flight per warp
+  int band_group;        // x: rows per group (worked on together by the warp's lanes)
   int band_seg;          // y / z: points per line segment (a multiple of 2 band_w + 1)
   // pointwise substep (x sweep only)
   const void* vx;
@@ -103,6 +104,8 @@ struct XItem {
   int slot;
   int nrow;
   long long row0;
+  int group;              // rows per group (<= BatchArgs::group_max)
+  int pad;
 };
 // One block of a batched y / z sweep: block blk of the nblk blocks of one slot.
 struct LineBlock {
@@ -116,7 +119,8 @@ struct BatchArgs {
   const SlotDesc* slots;
   const void* items;      // XItem (x) or LineBlock (y, z), one per warp / block
   int nitems;
-  int stages;             // x: rows in flight per warp
+  int stages;             // x: groups of rows in flight per warp
+  int group_max;          // x: row slots per stage (the largest group of the items)
   int slot_elems;         // x: shared-memory row slot, elements (>= pitch + 16 of every slot)
   int* status;
 };
@@ -149,7 +153,8 @@ cudaError_t launch_sweep_fast(int axis, const SweepParams& p, bool complex_field
 // FP32 banded x sweep: dynamic shared memory of a block of kBandWarps warps, one-time
 // preparation (shared-memory limit, resident blocks per SM) and launch on `grid` blocks.
 size_t x_band_smem(const SweepParams& p, bool complex_field);
-cudaError_t x_band_prepare(int w, bool complex_field, size_t smem, int* blocks_per_sm);
+cudaError_t x_band_prepare(int w, bool complex_field, bool grouped, size_t smem,
+                           int* blocks_per_sm);
 cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int grid,
                                 cudaStream_t st);
 // FP32 banded y / z sweeps (out of place like the streaming ones), blocks of 128 threads.
@@ -159,7 +164,10 @@ int band_line_blocks_per_sm(int axis, bool complex_field, int w);
 // Batched FP32 banded sweeps over the slots of a pool (one launch per direction
 // and mode): x on kBandWarps-warp blocks with dynamic shared memory
 // batch_x_smem(); y / z on blocks of 128 threads.  w is the launch half-width.
-size_t batch_x_smem(int stages, int slot_elems, bool complex_field);
+size_t batch_x_smem(int stages, int group_max, int slot_elems, bool complex_field);
+// Rows per group of the banded x sweep for rows of nx points (ept per 16-byte vector):
+// the cost model's best G in 1..8 whose stages fit warp_budget bytes of row slots.
+int x_band_group(int nx, int ept, int stages, size_t slot_bytes, size_t warp_budget);
 cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_blocks_per_sm);
 cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,
                                size_t smem, cudaStream_t st);

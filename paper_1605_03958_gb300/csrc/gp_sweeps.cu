@@ -797,8 +797,14 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
 // Needs nx >= kBandPad so that one reflection covers every window.
 constexpr int kBandPad = 8;     // room for the odd images on each side of a row slot
 
+__device__ __forceinline__ float shfl_e(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float2 shfl_e(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
 // What one warp of the banded x sweep works on: nrow consecutive rows from row0 of
-// one field, streamed through S shared-memory row slots of slot_elems elements each.
+// one field, taken G rows at a time (a group), streamed through S shared-memory
+// stages of G row slots of slot_elems elements each.
 template <class E> struct XRows {
   E* field;
   const float4* fx;      // trap factors along x, [pitch] (16-byte vectors)
@@ -807,22 +813,157 @@ template <class E> struct XRows {
   const double* scale;   // pending renormalisation factor
   int* status;
   long long row0;
-  int nrow, nx, pitch, S, slot_elems;
+  int nrow, nx, pitch, S, G, slot_elems;
   float dtg;             // dt g
 };
 
 // Barriers and ghost -1 of a warp's row slots (before the dependent-launch wait).
 template <class E>
-__device__ __forceinline__ void x_band_init(uint64_t* full, E* slots, int S, int slot_elems) {
+__device__ __forceinline__ void x_band_init(uint64_t* full, E* slots, int S, int nslots,
+                                            int slot_elems) {
   const int lane = threadIdx.x & 31;
   if (lane == 0)
     for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
-  if (lane < S) slots[(size_t)lane * slot_elems - 1] = E{};   // ghost -1 of every slot
+  for (int q = lane; q < nslots; q += 32) slots[(size_t)q * slot_elems - 1] = E{};   // ghost -1
   __syncwarp();
 }
 
 template <class R, bool CPLX, int W>
 __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>::E>& a,
+                                            uint64_t* full, typename Field<R, CPLX>::E* slots) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  constexpr int EPT = 16 / (int)sizeof(E);   // elements per 16-byte vector
+  constexpr int H = (W + EPT - 1) / EPT;     // halo vectors on each side of a window
+  constexpr int NV = 2 * H + 1;              // vectors in a window
+  static_assert(H * EPT <= kBandPad, "window inside the slot");
+  const int nx = a.nx, pitch = a.pitch, S = a.S, G = a.G, nrow = a.nrow, se = a.slot_elems;
+  const int lane = threadIdx.x & 31;
+  const int nvec = (nx + EPT - 1) / EPT;
+  const float inv_nvec = 1.0f / (float)nvec;
+  const int ngroups = (nrow + G - 1) / G;
+  const long long row0 = a.row0;
+  E* field = a.field;
+  const E* wt = a.wt;
+  const float4* fx = a.fx;
+  const E* fyz = a.fyz;
+  const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
+  const R s = (R)(*a.scale);
+  const R dtg = (R)a.dtg;
+  // row slot r of stage st
+  auto slot_of = [&](int st, int r) { return slots + (size_t)(st * G + r) * se; };
+  auto issue = [&](int i) {   // group i of this warp -> stage i % S, one bulk copy per row
+    const int st = i % S;
+    const int rows = min(G, nrow - i * G);
+    mbar_arrive_expect_tx(&full[st], (uint32_t)rows * rowbytes);
+    for (int r = 0; r < rows; ++r)
+      bulk_load(slot_of(st, r), field + (size_t)(row0 + (long long)i * G + r) * pitch, rowbytes,
+                &full[st]);
+  };
+  if (lane == 0)
+    for (int i = 0; i < S && i < ngroups; ++i) issue(i);
+  // trap factor of row `lane` of the current group, loaded one group ahead; a lane
+  // takes its row's factor from lane r by shuffle
+  E fcur = lane < min(G, nrow) ? fyz[row0 + lane] : F::zero();
+
+  for (int i = 0; i < ngroups; ++i) {
+    const int st = i % S;
+    const int rows = min(G, nrow - i * G);
+    const int nv = rows * nvec;            // vectors of the group
+    const long long gr0 = row0 + (long long)i * G;
+    const E fnext = (i + 1 < ngroups && lane < min(G, nrow - (i + 1) * G)) ? fyz[gr0 + G + lane] : F::zero();
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)(i / S) & 1u, kWaitLimitNs))) {
+      if (lane == 0) {
+        atomicOr(a.status, kStatusTimeout);
+        // wait (bounded) for every copy still in flight before the warp exits
+        for (int q = i; q < i + S && q < ngroups; ++q)
+          mbar_wait_bounded(&full[q % S], (uint32_t)(q / S) & 1u, kWaitLimitNs);
+      }
+      __syncwarp();
+      return;
+    }
+    // pointwise substep in place (past nx too: overwritten below); lanes run over the
+    // group's (row, vector) pairs and take the polynomial branch together when every
+    // argument of the warp allows it
+    for (int v0 = 0; v0 < nv; v0 += 32) {
+      const int idx = v0 + lane;
+      const bool act = idx < nv;
+      const int r = act ? (G == 1 ? 0 : __float2int_rz(((float)idx + 0.5f) * inv_nvec)) : 0;
+      const int v = act ? idx - r * nvec : 0;
+      float4* vp = reinterpret_cast<float4*>(slot_of(st, r) + v * EPT);
+      float4 raw = *vp;
+      const float4 fxv = __ldg(fx + v);
+      const E fr = shfl_e(fcur, r);
+      E* ev = reinterpret_cast<E*>(&raw);
+      const E* fe = reinterpret_cast<const E*>(&fxv);
+      R y[EPT];
+      R ymax = R(0);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        ev[e] = F::scaled(ev[e], s);
+        y[e] = dtg * F::abs2(ev[e]);
+        ymax = fmaxf(ymax, fabsf(y[e]));
+      }
+      if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_small(ev[e], F::mul(fe[e], fr), y[e]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_full(ev[e], F::mul(fe[e], fr), y[e]);
+      }
+      if (act) *vp = raw;
+    }
+    __syncwarp();
+    // per row: odd images about -1 (positions -2..-8) and about nx (nx+1..nx+7), and
+    // the ghost nx: 15 tasks
+    for (int t = lane; t < 15 * rows; t += 32) {
+      const int r = t / 15, k = t - 15 * r;
+      E* row = slot_of(st, r);
+      if (k < 7) row[-2 - k] = F::scaled(row[k], R(-1));
+      else if (k < 14) row[nx + 1 + (k - 7)] = F::scaled(row[nx - 1 - (k - 7)], R(-1));
+      else row[nx] = F::zero();
+    }
+    __syncwarp();
+    for (int idx = lane; idx < nv; idx += 32) {
+      const int r = G == 1 ? 0 : __float2int_rz(((float)idx + 0.5f) * inv_nvec);
+      const int v = idx - r * nvec;
+      const int x0 = v * EPT;
+      const float4* src = reinterpret_cast<const float4*>(slot_of(st, r) + x0 - H * EPT);
+      float4 wv[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) wv[q] = src[q];
+      const E* win = reinterpret_cast<const E*>(wv);
+      float4 ov;
+      E* o = reinterpret_cast<E*>(&ov);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int c = H * EPT + e;   // the output's position in the window
+        E acc = F::mul(wt[W], win[c]);
+#pragma unroll
+        for (int k = 1; k <= W; ++k) acc = F::chain(wt[W + k], F::add(win[c - k], win[c + k]), acc);
+        o[e] = F::add(win[c], acc);
+      }
+      E* grow = field + (size_t)(gr0 + r) * pitch;
+      if (x0 + EPT <= nx) {
+        *reinterpret_cast<float4*>(grow + x0) = ov;
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+          if (x0 + e < nx) grow[x0 + e] = o[e];
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && i + S < ngroups) {
+      fence_smem_to_async();
+      issue(i + S);
+    }
+    fcur = fnext;
+  }
+}
+
+// One row at a time (rows of 32 or more 16-byte vectors fill the lanes by themselves).
+template <class R, bool CPLX, int W>
+__device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R, CPLX>::E>& a,
                                             uint64_t* full, typename Field<R, CPLX>::E* slots) {
   using F = Field<R, CPLX>;
   using E = typename F::E;
@@ -938,18 +1079,18 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
   }
 }
 
-template <class R, bool CPLX, int W>
+template <class R, bool CPLX, int W, bool GROUPED>
 __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_constant__ SweepParams p) {
   using E = typename Field<R, CPLX>::E;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int S = p.band_stages, slot_elems = p.pitch + 2 * kBandPad;
+  const int S = p.band_stages, G = p.band_group, slot_elems = p.pitch + 2 * kBandPad;
   const int wib = threadIdx.x >> 5;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
-  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * slot_elems + kBandPad;
+  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * G * slot_elems + kBandPad;
   const long long nrows = (long long)p.ny * p.nz;
   const long long row0 = ((long long)blockIdx.x * kBandWarps + wib) * p.band_rows;
   const int nrow = (int)max(0LL, min((long long)p.band_rows, nrows - row0));
-  x_band_init(full, slots, S, slot_elems);
+  x_band_init(full, slots, S, S * G, slot_elems);
   pdl_begin();
   if (nrow == 0) return;
   XRows<E> a;
@@ -964,9 +1105,11 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.nx = p.nx;
   a.pitch = p.pitch;
   a.S = S;
+  a.G = G;
   a.slot_elems = slot_elems;
   a.dtg = (float)(p.dt * p.g);
-  x_band_rows<R, CPLX, W>(a, full, slots);
+  if (GROUPED) x_band_rows<R, CPLX, W>(a, full, slots);
+  else x_band_rows_single<R, CPLX, W>(a, full, slots);
 }
 
 // Batched x sweep: warp w of the launch takes work item w (rows of one slot).
@@ -974,12 +1117,14 @@ template <class R, bool CPLX, int W>
 __global__ void __launch_bounds__(32 * kBandWarps) k_batch_x_band(const __grid_constant__ BatchArgs b) {
   using E = typename Field<R, CPLX>::E;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int S = b.stages, slot_elems = b.slot_elems;
+  const int S = b.stages, GM = b.group_max, slot_elems = b.slot_elems;
   const int wib = threadIdx.x >> 5;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
-  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * slot_elems + kBandPad;
   const int w = blockIdx.x * kBandWarps + wib;
-  x_band_init(full, slots, S, slot_elems);
+  // the item's G rows of a stage sit in its first G of the GM slots per stage
+  const int G = w < b.nitems ? static_cast<const XItem*>(b.items)[w].group : 1;
+  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * GM * slot_elems + kBandPad;
+  x_band_init(full, slots, S, S * G, slot_elems);
   pdl_begin();
   if (w >= b.nitems) return;
   const XItem it = static_cast<const XItem*>(b.items)[w];
@@ -996,6 +1141,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_batch_x_band(const __grid_c
   a.nx = d.nx;
   a.pitch = d.pitch;
   a.S = S;
+  a.G = G;
   a.slot_elems = slot_elems;
   a.dtg = d.dtg;
   x_band_rows<R, CPLX, W>(a, full, slots);
@@ -1229,26 +1375,46 @@ int stream_warps_per_sm(int axis, bool complex_field, int trunc) {
   }
 }
 
-template <int W> static auto band_kernel(bool cplx) {
-  return cplx ? k_sweep_x_band<float, true, W> : k_sweep_x_band<float, false, W>;
+template <int W> static auto band_kernel(bool cplx, bool grouped) {
+  if (grouped) return cplx ? k_sweep_x_band<float, true, W, true> : k_sweep_x_band<float, false, W, true>;
+  return cplx ? k_sweep_x_band<float, true, W, false> : k_sweep_x_band<float, false, W, false>;
 }
 
-static void (*band_kernel_for(int w, bool cplx))(SweepParams) {
+static void (*band_kernel_for(int w, bool cplx, bool grouped))(SweepParams) {
   switch (w) {
-    case 3: return band_kernel<3>(cplx);
-    case 5: return band_kernel<5>(cplx);
-    case 8: return band_kernel<8>(cplx);
+    case 3: return band_kernel<3>(cplx, grouped);
+    case 5: return band_kernel<5>(cplx, grouped);
+    case 8: return band_kernel<8>(cplx, grouped);
     default: return nullptr;
   }
 }
 
 size_t x_band_smem(const SweepParams& p, bool complex_field) {
-  return 128 * kBandWarps + (size_t)kBandWarps * p.band_stages * (p.pitch + 2 * kBandPad) *
-                                (complex_field ? 8 : 4);
+  return 128 * kBandWarps + (size_t)kBandWarps * p.band_stages * p.band_group *
+                                (p.pitch + 2 * kBandPad) * (complex_field ? 8 : 4);
 }
 
-cudaError_t x_band_prepare(int w, bool complex_field, size_t smem, int* blocks_per_sm) {
-  void (*k)(SweepParams) = band_kernel_for(w, complex_field);
+int x_band_group(int nx, int ept, int stages, size_t slot_bytes, size_t warp_budget) {
+  // rows per group: cost per element of a group of G rows in warp instructions, from
+  // the measured split of the kernel (pointwise and dot products per 32 vectors, odd
+  // images per 32 of the 15 tasks per row, fixed work per group)
+  const int nvec = (nx + ept - 1) / ept;
+  int best = 1;
+  double best_cost = 1e300;
+  for (int g = 1; g <= 8; ++g) {
+    if (g > 1 && (size_t)stages * g * slot_bytes > warp_budget) break;
+    const double cost = (((g * nvec + 31) / 32) * 112.0 + ((15 * g + 31) / 32) * 15.0 + 40.0) /
+                        ((double)g * nx);
+    if (cost < best_cost * 0.98) {
+      best_cost = cost;
+      best = g;
+    }
+  }
+  return best;
+}
+
+cudaError_t x_band_prepare(int w, bool complex_field, bool grouped, size_t smem, int* blocks_per_sm) {
+  void (*k)(SweepParams) = band_kernel_for(w, complex_field, grouped);
   if (!k) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1257,7 +1423,7 @@ cudaError_t x_band_prepare(int w, bool complex_field, size_t smem, int* blocks_p
 
 cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int grid,
                                 cudaStream_t st) {
-  void (*k)(SweepParams) = band_kernel_for(p.band_w, complex_field);
+  void (*k)(SweepParams) = band_kernel_for(p.band_w, complex_field, p.band_group > 1);
   if (!k) return cudaErrorInvalidValue;
   return launch_pdl(k, grid, 32 * kBandWarps, x_band_smem(p, complex_field), st, p);
 }
@@ -1303,8 +1469,9 @@ cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_
   }
 }
 
-size_t batch_x_smem(int stages, int slot_elems, bool complex_field) {
-  return 128 * kBandWarps + (size_t)kBandWarps * stages * slot_elems * (complex_field ? 8 : 4);
+size_t batch_x_smem(int stages, int group_max, int slot_elems, bool complex_field) {
+  return 128 * kBandWarps +
+         (size_t)kBandWarps * stages * group_max * slot_elems * (complex_field ? 8 : 4);
 }
 
 template <int W> static cudaError_t batch_prepare_W(bool cplx, size_t x_smem, int* bps) {
