@@ -96,8 +96,8 @@ struct Layout {
   size_t off_field = 0, off_staging = 0, off_coef = 0, off_vtab = 0, off_otab = 0;
   size_t off_partials = 0, off_scalars = 0, total = 0;
   size_t coef_off[2][3][2] = {};   // [mode][axis][A/B] byte offset from off_coef
-  size_t fx_off[2] = {};           // FP32 trap factors along x per mode [pitch], from off_coef
-  size_t fyz_off[2] = {};          // FP32 trap factor per row per mode, from off_coef
+  size_t fx_off[2] = {};           // trap factors along x per mode [pitch], from off_coef
+  size_t fyz_off[2] = {};          // trap factor per row per mode, from off_coef
   size_t npartials = 0;
   SweepGeom geom[2][3];
   long long ntiles_z[2] = {0, 0};
@@ -194,13 +194,12 @@ const char* compute_layout(const gp_params* p, Layout* L) {
         L->coef_off[m][a][ab] = c;
         c = align_up(c + (size_t)n[a] * L->rbytes * (m + 1), kAlign);
       }
-  if (L->rbytes == 4)
-    for (int m = 0; m < 2; ++m) {
-      L->fx_off[m] = c;
-      c = align_up(c + (size_t)L->pitch[m] * 4 * (m + 1), kAlign);
-      L->fyz_off[m] = c;
-      c = align_up(c + rows * 4 * (m + 1), kAlign);
-    }
+  for (int m = 0; m < 2; ++m) {
+    L->fx_off[m] = c;
+    c = align_up(c + (size_t)L->pitch[m] * L->rbytes * (m + 1), kAlign);
+    L->fyz_off[m] = c;
+    c = align_up(c + rows * L->rbytes * (m + 1), kAlign);
+  }
   off = align_up(off + c, kAlign);
   L->off_vtab = off;
   off = align_up(off + (size_t)(p->nx + p->ny + p->nz) * L->rbytes, kAlign);
@@ -447,9 +446,9 @@ void fill_sweep_params(gp_solver* s) {
         long long blocks = (warps + 3) / 4;   // x: capped at the resident grid by the launcher
         s->fast_grid[m][a] = (int)blocks;
       }
+      q.band_fx = coef + s->L.fx_off[m];
+      q.band_fyz = coef + s->L.fyz_off[m];
       if (a == 0 && s->band_w[m][0]) {
-        q.band_fx = coef + s->L.fx_off[m];
-        q.band_fyz = coef + s->L.fyz_off[m];
         std::memcpy(q.band_wt, s->band_wt[m][0], sizeof q.band_wt);
         q.band_w = s->band_w[m][0];
         const size_t slot_bytes = ((size_t)s->L.pitch[m] + 16) * rb * (m + 1);
@@ -616,27 +615,28 @@ int upload_tables(gp_solver* s) {
       put<double>(buf, ot + iv * 8, V);
       put<double>(buf, ot + (ntot + iv) * 8, x * x);
     }
-  // FP32: trap factors of the pointwise substep, exp(-dt V) (real field) and
+  // trap factors of the pointwise substep, exp(-dt V) (real field) and
   // cis(-dt V) = (cos dt V, -sin dt V) (complex field), separable as a factor along x
-  // and one per row; computed in FP64, rounded once
-  if (!f64) {
+  // and one per row; computed in FP64, rounded once to the storage precision
+  {
+    const size_t rb = L.rbytes;
     auto pot = [&](int a, int i) {
       const double x = (i - 0.5 * (n[a] - 1)) * h[a];
       return 0.5 * w[a] * w[a] * x * x;
     };
     for (int i = 0; i < p.nx; ++i) {
       const double th = p.dt * pot(0, i);
-      put<float>(buf, L.fx_off[0] + (size_t)i * 4, (float)std::exp(-th));
-      put<float>(buf, L.fx_off[1] + (size_t)i * 8, (float)std::cos(th));
-      put<float>(buf, L.fx_off[1] + (size_t)i * 8 + 4, (float)-std::sin(th));
+      put_real(L.fx_off[0] + (size_t)i * rb, std::exp(-th));
+      put_real(L.fx_off[1] + (size_t)i * 2 * rb, std::cos(th));
+      put_real(L.fx_off[1] + (size_t)i * 2 * rb + rb, -std::sin(th));
     }
     for (int k = 0; k < p.nz; ++k)
       for (int j = 0; j < p.ny; ++j) {
         const double th = p.dt * (pot(1, j) + pot(2, k));
         const size_t r = (size_t)k * p.ny + j;
-        put<float>(buf, L.fyz_off[0] + r * 4, (float)std::exp(-th));
-        put<float>(buf, L.fyz_off[1] + r * 8, (float)std::cos(th));
-        put<float>(buf, L.fyz_off[1] + r * 8 + 4, (float)-std::sin(th));
+        put_real(L.fyz_off[0] + r * rb, std::exp(-th));
+        put_real(L.fyz_off[1] + r * 2 * rb, std::cos(th));
+        put_real(L.fyz_off[1] + r * 2 * rb + rb, -std::sin(th));
       }
   }
   GP_CUDA(s, cudaMemcpyAsync(s->base + L.off_coef, buf.data(), span, cudaMemcpyHostToDevice,

@@ -68,11 +68,22 @@ template <class R> struct Field<R, false> {
   static __device__ __forceinline__ E add(E a, E b) { return a + b; }
   static __device__ __forceinline__ R abs2(E v) { return v * v; }
   // v f exp(-y) with f = exp(-dt V) from the separable trap tables and y = dt g v^2:
-  // for |y| <= 1/16 exp(-y) by its Taylor polynomial of degree 4 (remainder below
-  // |y|^5/120 < 1e-8, under FP32 rounding), else by the library exp
+  // for |y| <= 1/16 exp(-y) by its Taylor polynomial, of degree 4 in FP32 (remainder
+  // below |y|^5/120 < 1e-8, under FP32 rounding) and 9 in FP64 (below |y|^10/10! <
+  // 3e-19, under FP64 rounding), else by the library exp
   static __device__ __forceinline__ E nonlinear_small(E v, E f, R y) {
     const R z = -y;
-    R q = fma(z, R(1.0 / 24.0), R(1.0 / 6.0));
+    R q;
+    if constexpr (sizeof(R) == 8) {
+      q = fma(z, R(1.0 / 362880.0), R(1.0 / 40320.0));
+      q = fma(z, q, R(1.0 / 5040.0));
+      q = fma(z, q, R(1.0 / 720.0));
+      q = fma(z, q, R(1.0 / 120.0));
+      q = fma(z, q, R(1.0 / 24.0));
+      q = fma(z, q, R(1.0 / 6.0));
+    } else {
+      q = fma(z, R(1.0 / 24.0), R(1.0 / 6.0));
+    }
     q = fma(z, q, R(0.5));
     q = fma(z, q, R(1));
     q = fma(z, q, R(1));
@@ -101,12 +112,23 @@ template <class R> struct Field<R, true> {
   static __device__ __forceinline__ E add(E a, E b) { return cadd(a, b); }
   static __device__ __forceinline__ R abs2(E v) { return fma(v.x, v.x, v.y * v.y); }
   // v f (cos th - i sin th) with f = cis(-dt V) from the separable trap tables and
-  // th = dt g |v|^2: for |th| <= 1/16 cos and sin by their Taylor polynomials of
-  // degrees 4 and 5 (remainders below th^6/720 and th^7/5040), else the library sincos
+  // th = dt g |v|^2: for |th| <= 1/16 cos and sin by their Taylor polynomials, of
+  // degrees 4 and 5 in FP32 (remainders below th^6/720 and th^7/5040) and 8 and 9 in
+  // FP64 (below th^10/10! and th^11/11!), else the library sincos
   static __device__ __forceinline__ E nonlinear_small(E v, E f, R th) {
     const R t2 = th * th;
-    const R cs = fma(t2, fma(t2, R(1.0 / 24.0), R(-0.5)), R(1));
-    const R sn = th * fma(t2, fma(t2, R(1.0 / 120.0), R(-1.0 / 6.0)), R(1));
+    R cs, sn;
+    if constexpr (sizeof(R) == 8) {
+      cs = fma(t2, R(1.0 / 40320.0), R(-1.0 / 720.0));
+      cs = fma(t2, cs, R(1.0 / 24.0));
+      sn = fma(t2, R(1.0 / 362880.0), R(-1.0 / 5040.0));
+      sn = fma(t2, sn, R(1.0 / 120.0));
+    } else {
+      cs = R(1.0 / 24.0);
+      sn = R(1.0 / 120.0);
+    }
+    cs = fma(t2, fma(t2, cs, R(-0.5)), R(1));
+    sn = th * fma(t2, fma(t2, sn, R(-1.0 / 6.0)), R(1));
     return cmul(cmul(v, f), E{cs, -sn});
   }
   static __device__ __forceinline__ E nonlinear_full(E v, E f, R th) {
@@ -151,10 +173,10 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
     const long long r = r0 + lane;
     const int j = (int)(r % p.ny);
     const int k = (int)(r / p.ny);
-    const R* vx = static_cast<const R*>(p.vx);
-    const R vyz = __ldg(static_cast<const R*>(p.vy) + j) + __ldg(static_cast<const R*>(p.vz) + k);
+    const E* fxt = static_cast<const E*>(p.band_fx);                      // trap factor along x
+    const E fr = __ldg(static_cast<const E*>(p.band_fyz) + (size_t)k * p.ny + j);   // of this row
     const R s = (R)(*p.scale);
-    const R dt = (R)p.dt, g = (R)p.g;
+    const R dtg = (R)(p.dt * p.g);
     const E* A = static_cast<const E*>(p.A);
     const E* B = static_cast<const E*>(p.B);
     const int head = p.head;
@@ -168,7 +190,10 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
     // element idx after the pending scale and the pointwise substep (0 outside)
     auto load = [&](int idx) -> E {
       if (idx < 0 || idx >= nx) return F::zero();
-      return F::pointwise(F::scaled(row[idx], s), __ldg(vx + idx) + vyz, dt, g);
+      const E v = F::scaled(row[idx], s);
+      const R y = dtg * F::abs2(v);
+      const E f = F::mul(__ldg(fxt + idx), fr);
+      return fabs(y) <= R(0.0625) ? F::nonlinear_small(v, f, y) : F::nonlinear_full(v, f, y);
     };
 
     E prev = F::zero(), dprev = F::zero();
