@@ -222,6 +222,19 @@ const char* gp_last_error(const gp_solver* s);
 /* Static text for a GP_* code. */
 const char* gp_strerror(int code);
 
+/* Physical units -> dimensionless nonlinearity (host only, no device).
+ * g = 4 pi N a_s / l_osc with the s-wave scattering length given in Bohr radii
+ * (a_0 = 5.29177210903e-11 m, CODATA 2018) and the oscillator length
+ * l_osc = sqrt(hbar / (m omega_x)) in metres, the x-oscillator unit of length of the
+ * equation's scaling.  natoms >= 0, a_s_bohr finite (negative: attractive),
+ * l_osc_m > 0; GP_ERR_ARG otherwise.                                              */
+int gp_units_g(double natoms, double a_s_bohr, double l_osc_m, double* g);
+
+/* Oscillator length l_osc = sqrt(hbar / (m omega)) in metres of an atom of mass
+ * mass_amu (unified atomic mass units, 1.66053906660e-27 kg) in a trap of angular
+ * frequency omega (rad/s; 2 pi nu for a trap frequency nu in Hz).                 */
+int gp_units_l_osc(double mass_amu, double omega, double* l_osc_m);
+
 /* ---------------------------------------------------------------- pools
  * A pool keeps many FP32 solves of different grids resident in one device arena and
  * steps them together: batched uneven solves and the serving loop.  Every live slot

@@ -831,6 +831,29 @@ int promote_to_complex(gp_solver* s) {
 
 extern "C" {
 
+int gp_units_g(double natoms, double a_s_bohr, double l_osc_m, double* g) {
+  constexpr double kBohr = 5.29177210903e-11;   // m, CODATA 2018
+  if (!g || !(natoms >= 0.0) || !std::isfinite(natoms) || !std::isfinite(a_s_bohr) ||
+      !(l_osc_m > 0.0) || !std::isfinite(l_osc_m)) {
+    g_create_error = "units: natoms >= 0, a_s finite and l_osc > 0 required";
+    return GP_ERR_ARG;
+  }
+  *g = 4.0 * kPi * natoms * (a_s_bohr * kBohr) / l_osc_m;
+  return GP_OK;
+}
+
+int gp_units_l_osc(double mass_amu, double omega, double* l_osc_m) {
+  constexpr double kHbar = 1.054571817e-34;     // J s (exact by the 2019 SI)
+  constexpr double kAmu = 1.66053906660e-27;    // kg, CODATA 2018
+  if (!l_osc_m || !(mass_amu > 0.0) || !std::isfinite(mass_amu) || !(omega > 0.0) ||
+      !std::isfinite(omega)) {
+    g_create_error = "units: mass and omega must be finite and > 0";
+    return GP_ERR_ARG;
+  }
+  *l_osc_m = std::sqrt(kHbar / (mass_amu * kAmu * omega));
+  return GP_OK;
+}
+
 int gp_workspace_bytes(const gp_params* p, size_t* bytes) {
   if (!bytes) {
     g_create_error = "bytes is NULL";

@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_observables_noalloc": (i, [vp, i, i, i, ll, i, i, d, d, d, d, d, d, d, vp, vp]),
         "gp_last_error": (ctypes.c_char_p, [vp]),
         "gp_strerror": (ctypes.c_char_p, [i]),
+        "gp_units_g": (i, [d, d, d, dp]),
+        "gp_units_l_osc": (i, [d, d, dp]),
         "gp_pool_slot_bytes": (i, [pp, ctypes.POINTER(ctypes.c_size_t)]),
         "gp_pool_create": (i, [ctypes.c_size_t, i, vp, ctypes.POINTER(vp)]),
         "gp_pool_destroy": (None, [vp]),
@@ -372,6 +374,22 @@ class Solver:
 
     def info(self):
         return gp_get_info(self.handle)
+
+
+# --------------------------------------------------------------------- units
+
+def gp_units_g(natoms: float, a_s_bohr: float, l_osc_m: float) -> float:
+    """g = 4 pi N a_s / l_osc, a_s in Bohr radii, l_osc in metres."""
+    v = ctypes.c_double()
+    _check(load_library().gp_units_g(float(natoms), float(a_s_bohr), float(l_osc_m), ctypes.byref(v)))
+    return v.value
+
+
+def gp_units_l_osc(mass_amu: float, omega: float) -> float:
+    """Oscillator length sqrt(hbar / (m omega)) in metres (mass in u, omega in rad/s)."""
+    v = ctypes.c_double()
+    _check(load_library().gp_units_l_osc(float(mass_amu), float(omega), ctypes.byref(v)))
+    return v.value
 
 
 # --------------------------------------------------------------------- pools

@@ -110,3 +110,26 @@ def test_pool_slot_bytes_on_the_host(P):
     with pytest.raises(P.GPError) as e:
         P.gp.gp_pool_slot_bytes(bad)
     assert e.value.code == P.gp.GP_ERR_ARG
+
+
+def test_units_helpers(P):
+    """Physical units -> g.  Pins independent of the formula's own constants: the
+    oscillator length of 87Rb (86.909 u) in a 2 pi x 100 Hz trap is 1.078 um (the
+    textbook value for rubidium in such a trap), and g is linear in N and a_s and
+    inversely proportional to l_osc; a_s given in metres through gp_params gives the
+    same g as a_s in Bohr radii through the helper."""
+    import math
+    l = P.gp.gp_units_l_osc(86.909, 2 * math.pi * 100.0)
+    assert abs(l - 1.0785e-6) / 1.0785e-6 < 1e-3
+    g1 = P.gp.gp_units_g(1e4, 100.0, l)
+    assert abs(P.gp.gp_units_g(2e4, 100.0, l) - 2 * g1) <= 1e-12 * g1
+    assert abs(P.gp.gp_units_g(1e4, 50.0, l) - g1 / 2) <= 1e-12 * g1
+    assert abs(P.gp.gp_units_g(1e4, 100.0, 2 * l) - g1 / 2) <= 1e-12 * g1
+    assert P.gp.gp_units_g(1e4, -10.0, l) < 0
+    # the same-unit path of gp_params: 4 pi N a_s / l_osc with a_s = 100 a0 in metres
+    assert abs(g1 - 4 * math.pi * 1e4 * 100 * 5.29177210903e-11 / l) <= 1e-12 * g1
+    for bad in ((-1.0, 100.0, l), (1e4, float("nan"), l), (1e4, 100.0, 0.0)):
+        with pytest.raises(P.GPError):
+            P.gp.gp_units_g(*bad)
+    with pytest.raises(P.GPError):
+        P.gp.gp_units_l_osc(0.0, 1.0)
