@@ -66,6 +66,10 @@ def lib() -> ctypes.CDLL:
         L.orc_step_imag.argtypes = [pp, dp, ctypes.c_long]
         L.orc_step_imag.restype = ctypes.c_int
         L.orc_step_real.argtypes = [pp, dp, ctypes.c_long]
+        L.orc_step_imag_strang.restype = ctypes.c_int
+        L.orc_step_imag_strang.argtypes = [pp, dp, ctypes.c_long]
+        L.orc_step_real_strang.restype = ctypes.c_int
+        L.orc_step_real_strang.argtypes = [pp, dp, ctypes.c_long]
         L.orc_step_real.restype = ctypes.c_int
         L.orc_observables.argtypes = [pp, dp, ctypes.c_int, dp]
         L.orc_observables.restype = None
@@ -157,6 +161,24 @@ def step_real(p: Problem, psi: np.ndarray, nsteps: int) -> np.ndarray:
     rc = lib().orc_step_real(ctypes.byref(p._c()), _dp(out), int(nsteps))
     if rc != 0:
         raise FloatingPointError(f"oracle real-time step failed ({rc})")
+    return out
+
+
+def step_imag_strang(p: Problem, psi: np.ndarray, nsteps: int) -> np.ndarray:
+    out = np.ascontiguousarray(psi, dtype=np.float64).copy()
+    assert out.shape == p.shape
+    rc = lib().orc_step_imag_strang(ctypes.byref(p._c()), _dp(out), int(nsteps))
+    if rc != 0:
+        raise FloatingPointError(f"oracle imaginary-time Strang step failed ({rc})")
+    return out
+
+
+def step_real_strang(p: Problem, psi: np.ndarray, nsteps: int) -> np.ndarray:
+    out = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    assert out.shape == p.shape
+    rc = lib().orc_step_real_strang(ctypes.byref(p._c()), _dp(out), int(nsteps))
+    if rc != 0:
+        raise FloatingPointError(f"oracle real-time Strang step failed ({rc})")
     return out
 
 

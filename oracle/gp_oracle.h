@@ -66,6 +66,11 @@ int orc_step_imag(const orc_problem* p, double* psi, long nsteps);
 /* nsteps real-time SSCN steps on a complex field psi[2*N] (interleaved re, im). */
 int orc_step_real(const orc_problem* p, double* psi, long nsteps);
 
+/* Strang-split variants: half pointwise substep, the three CN solves, half
+ * pointwise substep (then the renormalisation in imaginary time).                */
+int orc_step_imag_strang(const orc_problem* p, double* psi, long nsteps);
+int orc_step_real_strang(const orc_problem* p, double* psi, long nsteps);
+
 /* Observables of psi (real: N doubles; complex: 2N interleaved).
  * out[10] = norm, mu, energy, ekin, epot, eint, rms_x, rms_y, rms_z, rms_r.       */
 void orc_observables(const orc_problem* p, const double* psi, int is_complex, double* out);
