@@ -147,6 +147,17 @@ int gp_step_real(gp_solver* s, long nsteps);
  * by a factor).  Takes effect for the next step.                                 */
 int gp_set_g(gp_solver* s, double g);
 
+/* Splitting of one time step.  GP_SPLIT_LIE (default): the pointwise substep with the
+ * full dt, then the CN solves along x, y, z (one fused pass per axis).
+ * GP_SPLIT_STRANG: half pointwise substep, CN solves, half pointwise substep, each
+ * half taking |psi|^2 before its own update (second order in dt for the linear
+ * part, and time-reversible in real time).  In real time n Strang steps cost n Lie
+ * steps plus two pointwise passes (the inner halves merge exactly, the phase keeping
+ * |psi|); in imaginary time each step adds two pointwise passes and renormalises
+ * after the second.  Takes effect at the next step call.                          */
+enum { GP_SPLIT_LIE = 0, GP_SPLIT_STRANG = 1 };
+int gp_set_splitting(gp_solver* s, int scheme);
+
 /* Current g (after the physical-units conversion and any gp_set_g). */
 int gp_get_g(const gp_solver* s, double* g);
 

@@ -98,6 +98,8 @@ struct Layout {
   size_t coef_off[2][3][2] = {};   // [mode][axis][A/B] byte offset from off_coef
   size_t fx_off[2] = {};           // trap factors along x per mode [pitch], from off_coef
   size_t fyz_off[2] = {};          // trap factor per row per mode, from off_coef
+  size_t fxh_off[2] = {};          // the same for half a step (Strang splitting)
+  size_t fyzh_off[2] = {};
   size_t npartials = 0;
   SweepGeom geom[2][3];
   long long ntiles_z[2] = {0, 0};
@@ -194,12 +196,13 @@ const char* compute_layout(const gp_params* p, Layout* L) {
         L->coef_off[m][a][ab] = c;
         c = align_up(c + (size_t)n[a] * L->rbytes * (m + 1), kAlign);
       }
-  for (int m = 0; m < 2; ++m) {
-    L->fx_off[m] = c;
-    c = align_up(c + (size_t)L->pitch[m] * L->rbytes * (m + 1), kAlign);
-    L->fyz_off[m] = c;
-    c = align_up(c + rows * L->rbytes * (m + 1), kAlign);
-  }
+  for (int m = 0; m < 2; ++m)
+    for (int half = 0; half < 2; ++half) {
+      (half ? L->fxh_off : L->fx_off)[m] = c;
+      c = align_up(c + (size_t)L->pitch[m] * L->rbytes * (m + 1), kAlign);
+      (half ? L->fyzh_off : L->fyz_off)[m] = c;
+      c = align_up(c + rows * L->rbytes * (m + 1), kAlign);
+    }
   off = align_up(off + c, kAlign);
   L->off_vtab = off;
   off = align_up(off + (size_t)(p->nx + p->ny + p->nz) * L->rbytes, kAlign);
@@ -293,6 +296,8 @@ struct gp_solver {
   int trunc[2][3] = {};              // FP32 fast sweeps: truncation depth, 0 = use the tile kernel
   int fast_grid[2][3] = {};          // blocks of the fast sweeps (x band: persistent grid)
   int band_w[2][3] = {};             // FP32 banded sweep half-width per mode and axis, 0 = not used
+  int split = GP_SPLIT_LIE;          // splitting of a step
+  bool kinetic_only = false;         // x sweep without the pointwise substep (Strang)
   float band_wt[2][3][2 * 17] = {};  // its weights (complex: pairs)
   int nsm = 0;
   CUtensorMap tmap[2][3];  // [mode][axis]; axis 0 unused (64-byte aligned type)
@@ -401,6 +406,7 @@ void fill_sweep_params(gp_solver* s) {
       q.vz = vt + (size_t)(p.nx + p.ny) * rb;
       q.dt = p.dt;
       q.g = s->g;
+      q.pw = 1;
       q.scale = s->scale;
       q.partials = s->partials;
       q.counter = s->counters;
@@ -624,20 +630,25 @@ int upload_tables(gp_solver* s) {
       const double x = (i - 0.5 * (n[a] - 1)) * h[a];
       return 0.5 * w[a] * w[a] * x * x;
     };
-    for (int i = 0; i < p.nx; ++i) {
-      const double th = p.dt * pot(0, i);
-      put_real(L.fx_off[0] + (size_t)i * rb, std::exp(-th));
-      put_real(L.fx_off[1] + (size_t)i * 2 * rb, std::cos(th));
-      put_real(L.fx_off[1] + (size_t)i * 2 * rb + rb, -std::sin(th));
-    }
-    for (int k = 0; k < p.nz; ++k)
-      for (int j = 0; j < p.ny; ++j) {
-        const double th = p.dt * (pot(1, j) + pot(2, k));
-        const size_t r = (size_t)k * p.ny + j;
-        put_real(L.fyz_off[0] + r * rb, std::exp(-th));
-        put_real(L.fyz_off[1] + r * 2 * rb, std::cos(th));
-        put_real(L.fyz_off[1] + r * 2 * rb + rb, -std::sin(th));
+    for (int half = 0; half < 2; ++half) {
+      const double tau = half ? 0.5 * p.dt : p.dt;
+      const size_t* fxo = half ? L.fxh_off : L.fx_off;
+      const size_t* fyo = half ? L.fyzh_off : L.fyz_off;
+      for (int i = 0; i < p.nx; ++i) {
+        const double th = tau * pot(0, i);
+        put_real(fxo[0] + (size_t)i * rb, std::exp(-th));
+        put_real(fxo[1] + (size_t)i * 2 * rb, std::cos(th));
+        put_real(fxo[1] + (size_t)i * 2 * rb + rb, -std::sin(th));
       }
+      for (int k = 0; k < p.nz; ++k)
+        for (int j = 0; j < p.ny; ++j) {
+          const double th = tau * (pot(1, j) + pot(2, k));
+          const size_t r = (size_t)k * p.ny + j;
+          put_real(fyo[0] + r * rb, std::exp(-th));
+          put_real(fyo[1] + r * 2 * rb, std::cos(th));
+          put_real(fyo[1] + r * 2 * rb + rb, -std::sin(th));
+        }
+    }
   }
   GP_CUDA(s, cudaMemcpyAsync(s->base + L.off_coef, buf.data(), span, cudaMemcpyHostToDevice,
                              s->stream));
@@ -761,7 +772,8 @@ cudaEvent_t take_event(gp_solver* s) {
 
 template <class R> int run_sweep(gp_solver* s, int axis) {
   const int m = s->is_complex ? 1 : 0;
-  const SweepParams& q = s->sp[m][axis];
+  SweepParams q = s->sp[m][axis];
+  if (axis == 0 && s->kinetic_only) q.pw = 0;
   const size_t smem = s->L.geom[m][axis].smem;
   TimedLaunch tl{nullptr, nullptr, axis};
   if (s->timing) {
@@ -790,13 +802,64 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
   return GP_OK;
 }
 
-template <class R> int steps(gp_solver* s, long nsteps) {
+template <class R> int lie_steps(gp_solver* s, long nsteps) {
   for (long t = 0; t < nsteps; ++t)
     for (int a = 0; a < 3; ++a) {
       const int rc = run_sweep<R>(s, a);
       if (rc != GP_OK) return rc;
     }
   return GP_OK;
+}
+
+// One kinetic-only step: the three sweeps, the x sweep applying only the pending factor.
+template <class R> int kinetic_step(gp_solver* s) {
+  s->kinetic_only = true;
+  const int rc = lie_steps<R>(s, 1);
+  s->kinetic_only = false;
+  return rc;
+}
+
+int set_scale_one(gp_solver* s);
+
+// Half pointwise substep over the field (Strang): apply_scale applies the pending
+// factor first (and then resets it to 1 unless norm sets it); norm makes the result's
+// 1 / sqrt(norm) the pending factor.
+template <class R> int half_pointwise(gp_solver* s, bool apply_scale, bool norm) {
+  const int m = s->is_complex ? 1 : 0;
+  FieldParams f = field_params(s);
+  f.out = s->scale;
+  unsigned char* coef = s->base + s->L.off_coef;
+  cudaError_t e = gpk::launch_half_pointwise<R>(f, m == 1, coef + s->L.fxh_off[m],
+                                                coef + s->L.fyzh_off[m], 0.5 * s->prm.dt * s->g,
+                                                apply_scale, norm, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "half pointwise");
+  if (apply_scale && !norm) return set_scale_one(s);
+  return GP_OK;
+}
+
+// Strang steps psi <- P(dt/2) K(dt) P(dt/2) psi (imaginary time: then renormalised).
+// Real time: |psi| is invariant under the pointwise phase, so P(dt/2) P(dt/2) = P(dt)
+// and n steps are P(dt/2), K, n-1 fused Lie steps, P(dt/2).  Imaginary time: each
+// step is P(dt/2) (pending factor applied), K, P(dt/2) with its norm.
+template <class R> int strang_steps(gp_solver* s, long nsteps) {
+  if (nsteps == 0) return GP_OK;
+  int rc;
+  if (s->is_complex) {
+    if ((rc = half_pointwise<R>(s, true, false)) != GP_OK) return rc;
+    if ((rc = kinetic_step<R>(s)) != GP_OK) return rc;
+    if ((rc = lie_steps<R>(s, nsteps - 1)) != GP_OK) return rc;
+    return half_pointwise<R>(s, true, false);
+  }
+  for (long t = 0; t < nsteps; ++t) {
+    if ((rc = half_pointwise<R>(s, true, false)) != GP_OK) return rc;
+    if ((rc = kinetic_step<R>(s)) != GP_OK) return rc;
+    if ((rc = half_pointwise<R>(s, false, true)) != GP_OK) return rc;
+  }
+  return GP_OK;
+}
+
+template <class R> int steps(gp_solver* s, long nsteps) {
+  return s->split == GP_SPLIT_STRANG ? strang_steps<R>(s, nsteps) : lie_steps<R>(s, nsteps);
 }
 
 int check_status(gp_solver* s) {
@@ -955,6 +1018,14 @@ int gp_step_real(gp_solver* s, long nsteps) {
     if (rc != GP_OK) return rc;
   }
   return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
+}
+
+int gp_set_splitting(gp_solver* s, int scheme) {
+  if (!s) return GP_ERR_ARG;
+  if (scheme != GP_SPLIT_LIE && scheme != GP_SPLIT_STRANG)
+    return fail(s, GP_ERR_ARG, "scheme must be GP_SPLIT_LIE or GP_SPLIT_STRANG");
+  s->split = scheme;
+  return GP_OK;
 }
 
 int gp_set_g(gp_solver* s, double g) {

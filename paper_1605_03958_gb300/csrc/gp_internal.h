@@ -68,6 +68,7 @@ struct SweepParams {
   int band_group;        // x: rows per group (worked on together by the warp's lanes)
   int band_seg;          // y / z: points per line segment (a multiple of 2 band_w + 1)
   // pointwise substep (x sweep only)
+  int pw;                // 1: pointwise substep fused on load; 0: kinetic-only step
   const void* vx;
   const void* vy;
   const void* vz;
@@ -176,6 +177,13 @@ int stream_warps_per_sm(int axis, bool complex_field, int trunc);
 
 template <class R> cudaError_t launch_observables(const FieldParams& p, bool complex_field,
                                                   cudaStream_t st);
+// Standalone pointwise substep over the field (Strang splitting's half steps): trap
+// factors fx [pitch] and fyz [rows] of the half step, dtg = (dt / 2) g; the pending
+// factor *p.scale applied first when apply_scale; with norm, *p.out receives
+// 1 / sqrt(sum |psi|^2 dV) of the result (fixed-order FP64 sum).
+template <class R> cudaError_t launch_half_pointwise(const FieldParams& p, bool complex_field,
+                                                     const void* fx, const void* fyz, double dtg,
+                                                     bool apply_scale, bool norm, cudaStream_t st);
 template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaStream_t st);
 template <class R> cudaError_t launch_init_gaussian(const FieldParams& p, double wx, double wy,
                                                     double wz, cudaStream_t st);

@@ -158,6 +158,49 @@ __global__ void __launch_bounds__(kReduceThreads) k_norm_to_scale(const FieldPar
   }
 }
 
+// ------------------------------------------- standalone pointwise substep
+
+// psi <- P(psi) with the half step's separable trap factors and dtg = (dt / 2) g, the
+// same arithmetic as the sweeps' fused substep (Field policies); with NORM the norm
+// of the result becomes the pending factor.
+template <class R, bool CPLX, bool NORM>
+__global__ void __launch_bounds__(kReduceThreads) k_half_pointwise(const FieldParams p, const void* fx,
+                                                                   const void* fyz, double dtg_d,
+                                                                   int apply_scale) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  const int nx = p.nx;
+  const size_t P = (size_t)p.pitch;
+  const R s = apply_scale ? (R)(*p.scale) : R(1);
+  const R dtg = (R)dtg_d;
+  const E* fxt = static_cast<const E*>(fx);
+  const E* fyt = static_cast<const E*>(fyz);
+  E* psi = static_cast<E*>(p.psi);
+  double acc[1] = {0.0};
+  const long long nrows = (long long)p.ny * p.nz;
+  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const E fr = fyt[r];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const size_t idx = (size_t)r * P + i;
+      const E v = F::scaled(psi[idx], s);
+      const R y = dtg * F::abs2(v);
+      const E f = F::mul(fxt[i], fr);
+      const E u = fabs(y) <= R(0.0625) ? F::nonlinear_small(v, f, y) : F::nonlinear_full(v, f, y);
+      psi[idx] = u;
+      if (NORM) acc[0] += (double)F::abs2(u);
+    }
+  }
+  if (NORM) {
+    __shared__ double tot[1];
+    if (!block_reduce_last<1>(acc, p.partials, p.counter, tot)) return;
+    if (threadIdx.x == 0) {
+      const double norm = tot[0] * p.hx * p.hy * p.hz;
+      if (!(norm > 0.0) || !isfinite(norm)) atomicOr(p.status, kStatusNonFinite);
+      *p.out = 1.0 / sqrt(norm);
+    }
+  }
+}
+
 // ------------------------------------------------------------ initial Gaussian
 
 template <class R>
@@ -302,6 +345,21 @@ template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaSt
 }
 
 template <class R>
+cudaError_t launch_half_pointwise(const FieldParams& p, bool complex_field, const void* fx,
+                                  const void* fyz, double dtg, bool apply_scale, bool norm,
+                                  cudaStream_t st) {
+  const int as = apply_scale ? 1 : 0;
+  if (complex_field) {
+    if (norm) k_half_pointwise<R, true, true><<<kReduceBlocks, kReduceThreads, 0, st>>>(p, fx, fyz, dtg, as);
+    else k_half_pointwise<R, true, false><<<kReduceBlocks, kReduceThreads, 0, st>>>(p, fx, fyz, dtg, as);
+  } else {
+    if (norm) k_half_pointwise<R, false, true><<<kReduceBlocks, kReduceThreads, 0, st>>>(p, fx, fyz, dtg, as);
+    else k_half_pointwise<R, false, false><<<kReduceBlocks, kReduceThreads, 0, st>>>(p, fx, fyz, dtg, as);
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t launch_init_gaussian(const FieldParams& p, double wx, double wy, double wz,
                                  cudaStream_t st) {
   k_init_gaussian<R><<<grid_for_rows(p), 256, 0, st>>>(p, wx, wy, wz);
@@ -362,6 +420,8 @@ cudaError_t launch_cols_sum(const double* in, int rows, int cols, double w, doub
 #define GP_INSTANTIATE(R)                                                                      \
   template cudaError_t launch_observables<R>(const FieldParams&, bool, cudaStream_t);         \
   template cudaError_t launch_norm_to_scale<R>(const FieldParams&, cudaStream_t);             \
+  template cudaError_t launch_half_pointwise<R>(const FieldParams&, bool, const void*,       \
+                                                const void*, double, bool, bool, cudaStream_t); \
   template cudaError_t launch_init_gaussian<R>(const FieldParams&, double, double, double,    \
                                                cudaStream_t);                                  \
   template cudaError_t launch_import<R>(const FieldParams&, const double*, bool, cudaStream_t); \

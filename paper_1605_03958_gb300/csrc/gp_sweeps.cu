@@ -46,98 +46,6 @@ namespace gpk {
 
 constexpr int kU = 8;  // elements loaded ahead of the recurrence
 
-// ----------------------------------------------------------- field policies
-
-template <class R, bool CPLX> struct Field;
-
-// Real field, imaginary time.
-template <class R> struct Field<R, false> {
-  using E = R;
-  static __device__ __forceinline__ E zero() { return R(0); }
-  static __device__ __forceinline__ E scaled(E v, R s) { return v * s; }
-  // v exp(-dt (V + g v^2))
-  static __device__ __forceinline__ E pointwise(E v, R V, R dt, R g) {
-    return v * gp_exp(-dt * fma(g * v, v, V));
-  }
-  // off-chain part of the forward step: A v_j + B (v_{j-1} + v_{j+1})
-  static __device__ __forceinline__ E rhs(E A, E B, E prev, E next, E cur) {
-    return fma(B, prev + next, A * cur);
-  }
-  static __device__ __forceinline__ E chain(E B, E x, E c) { return fma(B, x, c); }
-  static __device__ __forceinline__ E mul(E a, E b) { return a * b; }
-  static __device__ __forceinline__ E add(E a, E b) { return a + b; }
-  static __device__ __forceinline__ R abs2(E v) { return v * v; }
-  // v f exp(-y) with f = exp(-dt V) from the separable trap tables and y = dt g v^2:
-  // for |y| <= 1/16 exp(-y) by its Taylor polynomial, of degree 4 in FP32 (remainder
-  // below |y|^5/120 < 1e-8, under FP32 rounding) and 9 in FP64 (below |y|^10/10! <
-  // 3e-19, under FP64 rounding), else by the library exp
-  static __device__ __forceinline__ E nonlinear_small(E v, E f, R y) {
-    const R z = -y;
-    R q;
-    if constexpr (sizeof(R) == 8) {
-      q = fma(z, R(1.0 / 362880.0), R(1.0 / 40320.0));
-      q = fma(z, q, R(1.0 / 5040.0));
-      q = fma(z, q, R(1.0 / 720.0));
-      q = fma(z, q, R(1.0 / 120.0));
-      q = fma(z, q, R(1.0 / 24.0));
-      q = fma(z, q, R(1.0 / 6.0));
-    } else {
-      q = fma(z, R(1.0 / 24.0), R(1.0 / 6.0));
-    }
-    q = fma(z, q, R(0.5));
-    q = fma(z, q, R(1));
-    q = fma(z, q, R(1));
-    return v * f * q;
-  }
-  static __device__ __forceinline__ E nonlinear_full(E v, E f, R y) { return v * f * gp_exp(-y); }
-};
-
-// Complex field, real time.
-template <class R> struct Field<R, true> {
-  using E = typename Cplx<R>::T;
-  static __device__ __forceinline__ E zero() { return E{R(0), R(0)}; }
-  static __device__ __forceinline__ E scaled(E v, R s) { return E{v.x * s, v.y * s}; }
-  // v exp(-i dt (V + g |v|^2)) = v (cos th - i sin th)
-  static __device__ __forceinline__ E pointwise(E v, R V, R dt, R g) {
-    const R th = dt * fma(g, fma(v.x, v.x, v.y * v.y), V);
-    R sn, cs;
-    gp_sincos(th, &sn, &cs);
-    return E{fma(v.x, cs, v.y * sn), fma(v.y, cs, -v.x * sn)};
-  }
-  static __device__ __forceinline__ E rhs(E A, E B, E prev, E next, E cur) {
-    return cfma(B, cadd(prev, next), cmul(A, cur));
-  }
-  static __device__ __forceinline__ E chain(E B, E x, E c) { return cfma(B, x, c); }
-  static __device__ __forceinline__ E mul(E a, E b) { return cmul(a, b); }
-  static __device__ __forceinline__ E add(E a, E b) { return cadd(a, b); }
-  static __device__ __forceinline__ R abs2(E v) { return fma(v.x, v.x, v.y * v.y); }
-  // v f (cos th - i sin th) with f = cis(-dt V) from the separable trap tables and
-  // th = dt g |v|^2: for |th| <= 1/16 cos and sin by their Taylor polynomials, of
-  // degrees 4 and 5 in FP32 (remainders below th^6/720 and th^7/5040) and 8 and 9 in
-  // FP64 (below th^10/10! and th^11/11!), else the library sincos
-  static __device__ __forceinline__ E nonlinear_small(E v, E f, R th) {
-    const R t2 = th * th;
-    R cs, sn;
-    if constexpr (sizeof(R) == 8) {
-      cs = fma(t2, R(1.0 / 40320.0), R(-1.0 / 720.0));
-      cs = fma(t2, cs, R(1.0 / 24.0));
-      sn = fma(t2, R(1.0 / 362880.0), R(-1.0 / 5040.0));
-      sn = fma(t2, sn, R(1.0 / 120.0));
-    } else {
-      cs = R(1.0 / 24.0);
-      sn = R(1.0 / 120.0);
-    }
-    cs = fma(t2, fma(t2, cs, R(-0.5)), R(1));
-    sn = th * fma(t2, fma(t2, sn, R(-1.0 / 6.0)), R(1));
-    return cmul(cmul(v, f), E{cs, -sn});
-  }
-  static __device__ __forceinline__ E nonlinear_full(E v, E f, R th) {
-    R sn, cs;
-    gp_sincos(th, &sn, &cs);
-    return cmul(cmul(v, f), E{cs, -sn});
-  }
-};
-
 template <class E>
 __device__ __forceinline__ E coef(const E* T, int j, int head, E bulk) {
   return j < head ? __ldg(T + j) : bulk;
@@ -191,6 +99,7 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
     auto load = [&](int idx) -> E {
       if (idx < 0 || idx >= nx) return F::zero();
       const E v = F::scaled(row[idx], s);
+      if (!p.pw) return v;   // kinetic-only step
       const R y = dtg * F::abs2(v);
       const E f = F::mul(__ldg(fxt + idx), fr);
       return fabs(y) <= R(0.0625) ? F::nonlinear_small(v, f, y) : F::nonlinear_full(v, f, y);
@@ -719,6 +628,7 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
     const int j = c * C + u;
     if (j >= nx) return F::zero();
     const E raw = ib[(c % 3) * 32 * kXS + lane * kXS + u];
+    if (!p.pw) return F::scaled(raw, s);   // kinetic-only step
     return F::pointwise(F::scaled(raw, s), __ldg(vx + j) + vyz, dt, g);
   };
 
@@ -839,6 +749,7 @@ template <class E> struct XRows {
   int* status;
   long long row0;
   int nrow, nx, pitch, S, G, slot_elems;
+  int pw;                // 1: pointwise substep on load; 0: only the pending factor
   float dtg;             // dt g
 };
 
@@ -929,7 +840,9 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
         y[e] = dtg * F::abs2(ev[e]);
         ymax = fmaxf(ymax, fabsf(y[e]));
       }
-      if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
+      if (!a.pw) {
+        // kinetic-only step: the pending factor alone
+      } else if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_small(ev[e], F::mul(fe[e], fr), y[e]);
       } else {
@@ -1050,7 +963,9 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
         y[e] = dtg * F::abs2(ev[e]);
         ymax = fmaxf(ymax, fabsf(y[e]));
       }
-      if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
+      if (!a.pw) {
+        // kinetic-only step: the pending factor alone
+      } else if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_small(ev[e], F::mul(fe[e], fr), y[e]);
       } else {
@@ -1132,6 +1047,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.S = S;
   a.G = G;
   a.slot_elems = slot_elems;
+  a.pw = p.pw;
   a.dtg = (float)(p.dt * p.g);
   if (GROUPED) x_band_rows<R, CPLX, W>(a, full, slots);
   else x_band_rows_single<R, CPLX, W>(a, full, slots);
@@ -1168,6 +1084,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_batch_x_band(const __grid_c
   a.S = S;
   a.G = G;
   a.slot_elems = slot_elems;
+  a.pw = 1;
   a.dtg = d.dtg;
   x_band_rows<R, CPLX, W>(a, full, slots);
 }

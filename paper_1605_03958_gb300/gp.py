@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_step_imag": (i, [vp, l]),
         "gp_step_real": (i, [vp, l]),
         "gp_set_g": (i, [vp, d]),
+        "gp_set_splitting": (i, [vp, i]),
         "gp_get_g": (i, [vp, dp]),
         "gp_observables": (i, [vp, ctypes.POINTER(GpObs)]),
         "gp_density1d": (i, [vp, i, dp]),
@@ -205,6 +206,14 @@ def gp_step_real(h, nsteps: int) -> None:
 
 def gp_set_g(h, g: float) -> None:
     _check(load_library().gp_set_g(h, float(g)), h)
+
+
+GP_SPLIT_LIE = 0
+GP_SPLIT_STRANG = 1
+
+
+def gp_set_splitting(h, scheme: int) -> None:
+    _check(load_library().gp_set_splitting(h, int(scheme)), h)
 
 
 def gp_get_g(h) -> float:
@@ -355,6 +364,9 @@ class Solver:
 
     def set_g(self, g):
         gp_set_g(self.handle, g)
+
+    def set_splitting(self, scheme: str):
+        gp_set_splitting(self.handle, {"lie": GP_SPLIT_LIE, "strang": GP_SPLIT_STRANG}[scheme])
 
     def get_g(self):
         return gp_get_g(self.handle)
