@@ -30,6 +30,10 @@
  *         solved by the Thomas recurrence with precomputed elimination coefficients;
  *     (3) imaginary time only: psi <- psi / sqrt(sum |psi|^2 dV).
  *   Grid: x_i = (i - (n-1)/2) h, every stored point an unknown, psi = 0 on the ghosts.
+ *   2D (the imag2d / real2d programs; nz = 1): the same equation in the xy plane,
+ *   V = (gamma^2 x^2 + nu^2 y^2) / 2, CN solves along x and y only, dV = hx hy; g is
+ *   then the 2D nonlinearity (the paper does not print its reduction from the 3D
+ *   inputs).
  */
 #include "gp_oracle.h"
 
@@ -70,6 +74,10 @@ static void sum_add(orc_sum* a, double x) {
 static double sum_val(const orc_sum* a) { return a->s + a->c; }
 
 static long npoints(const orc_problem* p) { return (long)p->nx * p->ny * p->nz; }
+
+/* nz = 1 is a 2D problem in the xy plane: no z solve, cell area hx hy, z = 0. */
+static int is2d(const orc_problem* p) { return p->nz == 1; }
+static double cell(const orc_problem* p) { return p->hx * p->hy * (is2d(p) ? 1.0 : p->hz); }
 
 static long index3(const orc_problem* p, int i, int j, int k) {
   return ((long)k * p->ny + j) * p->nx + i;
@@ -241,7 +249,7 @@ static double norm_of(const orc_problem* p, const double* psi, int is_complex) {
   orc_sum s = {0.0, 0.0};
   long n = npoints(p);
   for (long idx = 0; idx < n; ++idx) sum_add(&s, abs2(value(psi, is_complex, idx)));
-  return sum_val(&s) * p->hx * p->hy * p->hz;
+  return sum_val(&s) * cell(p);
 }
 
 void orc_init_gaussian(const orc_problem* p, double wx, double wy, double wz, double* psi) {
@@ -274,7 +282,7 @@ int orc_step_imag(const orc_problem* p, double* psi, long nsteps) {
     /* (2) CN kinetic solves along x, y, z with al = dt / (4 h^2) */
     sweep_real(p, psi, 0, p->dt / (4.0 * p->hx * p->hx));
     sweep_real(p, psi, 1, p->dt / (4.0 * p->hy * p->hy));
-    sweep_real(p, psi, 2, p->dt / (4.0 * p->hz * p->hz));
+    if (!is2d(p)) sweep_real(p, psi, 2, p->dt / (4.0 * p->hz * p->hz));
     /* (3) renormalise to unit norm */
     double nrm = norm_of(p, psi, 0);
     if (!(nrm > 0.0) || !isfinite(nrm)) return -4;
@@ -299,7 +307,7 @@ int orc_step_real(const orc_problem* p, double* psi_interleaved, long nsteps) {
     /* (2) CN kinetic solves along x, y, z with al = i dt / (4 h^2) */
     sweep_complex(p, psi, 0, I * (p->dt / (4.0 * p->hx * p->hx)));
     sweep_complex(p, psi, 1, I * (p->dt / (4.0 * p->hy * p->hy)));
-    sweep_complex(p, psi, 2, I * (p->dt / (4.0 * p->hz * p->hz)));
+    if (!is2d(p)) sweep_complex(p, psi, 2, I * (p->dt / (4.0 * p->hz * p->hz)));
   }
   for (long idx = 0; idx < npoints(p); ++idx)
     if (!isfinite(creal(psi[idx])) || !isfinite(cimag(psi[idx]))) return -4;
@@ -340,7 +348,7 @@ int orc_step_imag_strang(const orc_problem* p, double* psi, long nsteps) {
     half_pointwise_real(p, psi);
     sweep_real(p, psi, 0, p->dt / (4.0 * p->hx * p->hx));
     sweep_real(p, psi, 1, p->dt / (4.0 * p->hy * p->hy));
-    sweep_real(p, psi, 2, p->dt / (4.0 * p->hz * p->hz));
+    if (!is2d(p)) sweep_real(p, psi, 2, p->dt / (4.0 * p->hz * p->hz));
     half_pointwise_real(p, psi);
     double nrm = norm_of(p, psi, 0);
     if (!(nrm > 0.0) || !isfinite(nrm)) return -4;
@@ -356,7 +364,7 @@ int orc_step_real_strang(const orc_problem* p, double* psi_interleaved, long nst
     half_pointwise_complex(p, psi);
     sweep_complex(p, psi, 0, I * (p->dt / (4.0 * p->hx * p->hx)));
     sweep_complex(p, psi, 1, I * (p->dt / (4.0 * p->hy * p->hy)));
-    sweep_complex(p, psi, 2, I * (p->dt / (4.0 * p->hz * p->hz)));
+    if (!is2d(p)) sweep_complex(p, psi, 2, I * (p->dt / (4.0 * p->hz * p->hz)));
     half_pointwise_complex(p, psi);
   }
   for (long idx = 0; idx < npoints(p); ++idx)
@@ -408,12 +416,12 @@ void orc_observables(const orc_problem* p, const double* psi, int is_complex, do
         sum_add(&sy, y * y * d);
         sum_add(&sz, z * z * d);
       }
-  double dV = p->hx * p->hy * p->hz;
+  double dV = cell(p);
   double norm = sum_val(&nrm) * dV;
   double ekin = 0.5 * dV *
                 (edge_sum(p, psi, is_complex, 0) / (p->hx * p->hx) +
                  edge_sum(p, psi, is_complex, 1) / (p->hy * p->hy) +
-                 edge_sum(p, psi, is_complex, 2) / (p->hz * p->hz));
+                 (is2d(p) ? 0.0 : edge_sum(p, psi, is_complex, 2) / (p->hz * p->hz)));
   double epot = sum_val(&ep) * dV;
   double eint = 0.5 * p->g * sum_val(&e4) * dV;
   double x2 = sum_val(&sx) * dV / norm;
@@ -436,7 +444,8 @@ void orc_observables(const orc_problem* p, const double* psi, int is_complex, do
 void orc_density1d(const orc_problem* p, const double* psi, int is_complex, int axis,
                    double* out) {
   int n = axis == 0 ? p->nx : axis == 1 ? p->ny : p->nz;
-  double w = axis == 0 ? p->hy * p->hz : axis == 1 ? p->hx * p->hz : p->hx * p->hy;
+  const double hz = is2d(p) ? 1.0 : p->hz;
+  double w = axis == 0 ? p->hy * hz : axis == 1 ? p->hx * hz : p->hx * p->hy;
   orc_sum* s = calloc(n, sizeof(orc_sum));
   for (int k = 0; k < p->nz; ++k)
     for (int j = 0; j < p->ny; ++j)
@@ -452,7 +461,7 @@ void orc_density2d(const orc_problem* p, const double* psi, int is_complex, int 
                    double* out) {
   long n = plane == 0 ? (long)p->nx * p->ny : plane == 1 ? (long)p->nx * p->nz
                                                          : (long)p->ny * p->nz;
-  double w = plane == 0 ? p->hz : plane == 1 ? p->hy : p->hx;
+  double w = plane == 0 ? (is2d(p) ? 1.0 : p->hz) : plane == 1 ? p->hy : p->hx;
   orc_sum* s = calloc(n, sizeof(orc_sum));
   for (int k = 0; k < p->nz; ++k)
     for (int j = 0; j < p->ny; ++j)

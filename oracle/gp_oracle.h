@@ -27,7 +27,8 @@ extern "C" {
 /* Problem on an nx*ny*nz grid, layout psi[k][j][i] (x fastest), index
  * (k*ny + j)*nx + i.  Coordinates x_i = (i - (nx-1)/2) * hx (box centred on the
  * origin), same for y and z.  Homogeneous Dirichlet ghosts just outside the box.
- * Trap V = (gamma^2 x^2 + nu^2 y^2 + lambda^2 z^2) / 2.                          */
+ * Trap V = (gamma^2 x^2 + nu^2 y^2 + lambda^2 z^2) / 2.  nz = 1 is a 2D problem in
+ * the xy plane: z = 0, no z solve, cell area hx hy in every sum.                 */
 typedef struct {
   int nx, ny, nz;
   double hx, hy, hz;
