@@ -68,7 +68,10 @@ extern "C" {
 typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_prec;
 
 /* Problem definition ("Summary of revisions": physical inputs, trap anisotropy).
- *   nx, ny, nz     grid points per axis, each 3..2048
+ *   nx, ny, nz     grid points per axis, each 3..2048; nz = 1 makes a 2D solve in
+ *                  the xy plane (the imag2d / real2d programs): z = 0, no z solve,
+ *                  cell area dx dy in every sum, g the 2D nonlinearity, dz and lambda
+ *                  unused; rms_z is then 0
  *   dx, dy, dz     grid spacings (> 0), dimensionless (units of the x oscillator length)
  *   dt             time step (> 0)
  *   gamma, nu, lambda  trap frequencies relative to the x trap (> 0)

@@ -120,7 +120,8 @@ const char* check_params(const gp_params* p) {
   if (!p) return "params is NULL";
   const int n[3] = {p->nx, p->ny, p->nz};
   for (int a = 0; a < 3; ++a)
-    if (n[a] < 3 || n[a] > gpk::kMaxExtent) return "grid extents must be within 3..2048";
+    if ((n[a] < 3 && !(a == 2 && n[a] == 1)) || n[a] > gpk::kMaxExtent)
+      return "grid extents must be within 3..2048 (nz = 1: a 2D solve)";
   const double h[3] = {p->dx, p->dy, p->dz};
   for (int a = 0; a < 3; ++a)
     if (!(h[a] > 0.0) || !std::isfinite(h[a])) return "grid spacings must be finite and > 0";
@@ -340,7 +341,7 @@ FieldParams field_params(gp_solver* s) {
   f.tab = s->otab;
   f.hx = s->prm.dx;
   f.hy = s->prm.dy;
-  f.hz = s->prm.dz;
+  f.hz = s->prm.nz == 1 ? 1.0 : s->prm.dz;   // 2D: cell area hx hy
   f.g = s->g;
   return f;
 }
@@ -602,6 +603,9 @@ int upload_tables(gp_solver* s) {
         }
       }
     }
+  // 2D (nz = 1): no z sweep, so no out-of-place y / z pair either
+  if (p.nz == 1)
+    for (int m = 0; m < 2; ++m) s->trunc[m][2] = s->band_w[m][2] = 0;
   // the FP32 y / z kernels (banded or streaming) write out of place (y: field ->
   // staging, z: staging -> field), so they are used together or not at all
   for (int m = 0; m < 2; ++m)
@@ -803,8 +807,19 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
 }
 
 template <class R> int lie_steps(gp_solver* s, long nsteps) {
+  const bool two_d = s->prm.nz == 1;
   for (long t = 0; t < nsteps; ++t)
     for (int a = 0; a < 3; ++a) {
+      if (a == 2 && two_d) {
+        // 2D: no z sweep; imaginary time renormalises with a norm pass over the plane
+        if (!s->is_complex) {
+          FieldParams f = field_params(s);
+          f.out = s->scale;
+          const cudaError_t e = gpk::launch_norm_to_scale<R>(f, s->stream);
+          if (e != cudaSuccess) return cuda_fail(s, e, "norm");
+        }
+        continue;
+      }
       const int rc = run_sweep<R>(s, a);
       if (rc != GP_OK) return rc;
     }

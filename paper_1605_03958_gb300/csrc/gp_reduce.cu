@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_observables(const FieldParam
     const double epot = tot[1] * dV;
     const double eint = 0.5 * p.g * tot[2] * dV;
     const double ekin =
-        0.5 * dV * (tot[3] / (p.hx * p.hx) + tot[4] / (p.hy * p.hy) + tot[5] / (p.hz * p.hz));
+        0.5 * dV * (tot[3] / (p.hx * p.hx) + tot[4] / (p.hy * p.hy) +
+                    (p.nz == 1 ? 0.0 : tot[5] / (p.hz * p.hz)));   // 2D: no z kinetic term
     const double x2 = tot[6] * dV / norm, y2 = tot[7] * dV / norm, z2 = tot[8] * dV / norm;
     double* o = p.out;
     o[0] = norm;
