@@ -603,12 +603,13 @@ int upload_tables(gp_solver* s) {
         }
       }
     }
-  // 2D (nz = 1): no z sweep, so no out-of-place y / z pair either
+  // 2D (nz = 1): no z sweep; a fast (out-of-place) y sweep is followed by a copy of
+  // the staging area back to the field
   if (p.nz == 1)
     for (int m = 0; m < 2; ++m) s->trunc[m][2] = s->band_w[m][2] = 0;
   // the FP32 y / z kernels (banded or streaming) write out of place (y: field ->
-  // staging, z: staging -> field), so they are used together or not at all
-  for (int m = 0; m < 2; ++m)
+  // staging, z: staging -> field), so in 3D they are used together or not at all
+  for (int m = 0; m < 2 && p.nz > 1; ++m)
     if (!(s->trunc[m][1] || s->band_w[m][1]) || !(s->trunc[m][2] || s->band_w[m][2])) {
       s->trunc[m][1] = s->trunc[m][2] = 0;
       s->band_w[m][1] = s->band_w[m][2] = 0;
@@ -811,7 +812,13 @@ template <class R> int lie_steps(gp_solver* s, long nsteps) {
   for (long t = 0; t < nsteps; ++t)
     for (int a = 0; a < 3; ++a) {
       if (a == 2 && two_d) {
-        // 2D: no z sweep; imaginary time renormalises with a norm pass over the plane
+        // 2D: no z sweep.  A fast y sweep wrote the staging area: copy it back; then
+        // imaginary time renormalises with a norm pass over the plane
+        const int m = s->is_complex ? 1 : 0;
+        if (s->sp[m][1].trunc || s->sp[m][1].band_w)
+          GP_CUDA(s, cudaMemcpyAsync(s->field, s->staging,
+                                     (size_t)s->L.pitch[m] * s->L.rbytes * (m + 1) * s->prm.ny,
+                                     cudaMemcpyDeviceToDevice, s->stream));
         if (!s->is_complex) {
           FieldParams f = field_params(s);
           f.out = s->scale;

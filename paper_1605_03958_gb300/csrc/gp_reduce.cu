@@ -31,7 +31,8 @@ __device__ __forceinline__ double dabs2_diff(double2 a, double2 b) {
 
 // Fixed-order block sum of NACC accumulators into partials[blockIdx.x * NACC + c];
 // returns true in the last block to finish, after its fixed-order total over all
-// blocks has been written to tot[0..NACC-1] (shared memory).
+// blocks has been written to tot[0..NACC-1] (shared memory).  Every thread of every
+// block must call it.
 template <int NACC>
 __device__ bool block_reduce_last(double (&acc)[NACC], double* partials, unsigned int* counter,
                                   double* tot) {
@@ -56,15 +57,29 @@ __device__ bool block_reduce_last(double (&acc)[NACC], double* partials, unsigne
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  if (threadIdx.x < NACC) {
-    double s = 0.0, comp = 0.0;  // Neumaier over the blocks, in block order
-    for (unsigned int b = 0; b < gridDim.x; ++b) {
-      const double x = __ldcg(partials + (size_t)b * NACC + threadIdx.x);
+  // the blocks' partials of each accumulator: thread t takes blocks t, t + T, ...
+  // (Neumaier), then a shuffle tree and the warps in order -- a fixed order, and
+  // short FP64 dependency chains (one thread walking all blocks would take a chain
+  // of four FP64 operations per block)
+  const unsigned int nb = gridDim.x;
+#pragma unroll
+  for (int c = 0; c < NACC; ++c) {
+    double s = 0.0, comp = 0.0;
+    for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const double x = __ldcg(partials + (size_t)b * NACC + c);
       const double u = s + x;
       comp += (fabs(s) >= fabs(x)) ? (s - u) + x : (x - u) + s;
       s = u;
     }
-    tot[threadIdx.x] = s + comp;
+    double v = s + comp;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) warp_part[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NACC) {
+    double v = 0.0;
+    for (int w = 0; w < kReduceThreads / 32; ++w) v += warp_part[w][threadIdx.x];
+    tot[threadIdx.x] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
@@ -178,18 +193,37 @@ __global__ void __launch_bounds__(kReduceThreads) k_half_pointwise(const FieldPa
   const E* fyt = static_cast<const E*>(fyz);
   E* psi = static_cast<E*>(p.psi);
   double acc[1] = {0.0};
+  // chunks of CH rows, the chunk's CH * nx points spread over the block, U per thread
+  // in flight: all U loads are issued before any store
+  constexpr int U = 4, CH = 8;
   const long long nrows = (long long)p.ny * p.nz;
-  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
-    const E fr = fyt[r];
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const size_t idx = (size_t)r * P + i;
-      const E v = F::scaled(psi[idx], s);
-      const R y = dtg * F::abs2(v);
-      const E f = F::mul(fxt[i], fr);
-      const E u = fabs(y) <= R(0.0625) ? F::nonlinear_small(v, f, y) : F::nonlinear_full(v, f, y);
-      psi[idx] = u;
-      if (NORM) acc[0] += (double)F::abs2(u);
+  const int per = CH * nx;   // points per chunk
+  for (long long r0 = (long long)blockIdx.x * CH; r0 < nrows; r0 += (long long)gridDim.x * CH) {
+    const int rows = (int)min((long long)CH, nrows - r0);
+    const int cnt = rows * nx;
+    for (int base = threadIdx.x; base < cnt; base += blockDim.x * U) {
+      E v[U], f[U];
+      size_t at[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * blockDim.x;
+        const int q = e < cnt ? e : 0;
+        const int rl = q / nx, i = q - rl * nx;
+        at[u] = (size_t)(r0 + rl) * P + i;
+        v[u] = psi[at[u]];
+        f[u] = F::mul(fxt[i], fyt[r0 + rl]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (base + u * (int)blockDim.x >= cnt) continue;
+        const E w = F::scaled(v[u], s);
+        const R y = dtg * F::abs2(w);
+        const E out = fabs(y) <= R(0.0625) ? F::nonlinear_small(w, f[u], y) : F::nonlinear_full(w, f[u], y);
+        psi[at[u]] = out;
+        if (NORM) acc[0] += (double)F::abs2(out);
+      }
     }
+    (void)per;
   }
   if (NORM) {
     __shared__ double tot[1];
