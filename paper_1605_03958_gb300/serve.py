@@ -36,7 +36,8 @@ class Server:
         self.pool = Pool(arena_bytes, max_slots)
         self.quantum = int(quantum)
         self.tune = tune
-        self.stats = {"quanta": 0, "steps": 0, "admitted": 0, "max_live": 0}
+        self.stats = {"quanta": 0, "steps": 0, "admitted": 0, "max_live": 0,
+                      "step_s": 0.0, "admit_s": 0.0, "retire_s": 0.0, "live_sum": 0}
 
     def close(self):
         self.pool.close()
@@ -71,6 +72,7 @@ class Server:
             t = now()
             while pending and pending[0]["arrival"] <= t:
                 waiting.append(pending.popleft())
+            ta = time.perf_counter()
             while waiting:
                 try:
                     rec = self._admit(waiting[0], t)
@@ -81,6 +83,7 @@ class Server:
                 waiting.popleft()
                 live[rec["slot"]] = rec
                 self.stats["admitted"] += 1
+            self.stats["admit_s"] += time.perf_counter() - ta
             if not live:
                 if pending:   # idle until the next arrival
                     nxt = pending[0]["arrival"]
@@ -95,12 +98,16 @@ class Server:
                 tuned = True
             self.stats["max_live"] = max(self.stats["max_live"], len(live))
             q = min(self.quantum, min(r["remaining"] for r in live.values()))
+            ts = time.perf_counter()
             self.pool.step(q)
+            self.stats["step_s"] += time.perf_counter() - ts
             self.stats["quanta"] += 1
             self.stats["steps"] += q
+            self.stats["live_sum"] += len(live)
             if not realtime:
                 vnow += q * virtual_step_s
             t = now()
+            tr = time.perf_counter()
             for slot in [s for s, r in live.items() if r["remaining"] == q]:
                 r = live.pop(slot)
                 obs = self.pool.observables(slot)
@@ -113,6 +120,7 @@ class Server:
                     on_done(out)
             for r in live.values():
                 r["remaining"] -= q
+            self.stats["retire_s"] += time.perf_counter() - tr
         return done
 
 
