@@ -281,30 +281,36 @@ def run_cuda(args):
                 if peak_kind == "measured" else "fallback 6.8 TB/s"}
 
     # end to end through the public API: H2D of the step's input field from pinned
-    # host memory, one step, D2H of the resulting field into pinned host memory
+    # host memory, one step, D2H of the resulting field into pinned host memory; the
+    # host buffers are in the field's own precision (FP32 I/O for an FP32 solve)
     e2e = None
     if args.e2e_steps > 0:
-        host_in = torch.empty(NPTS, dtype=torch.float64, pin_memory=True)
-        host_out = torch.empty(NPTS, dtype=torch.float64, pin_memory=True)
-        P.gp.gp_get_psi_ptr(s.handle, host_in.data_ptr(), False)
+        f32 = sbytes == 4
+        hdt = torch.float32 if f32 else torch.float64
+        put = P.gp.gp_set_psi_f32_ptr if f32 else P.gp.gp_set_psi_ptr
+        get = P.gp.gp_get_psi_f32_ptr if f32 else P.gp.gp_get_psi_ptr
+        host_in = torch.empty(NPTS, dtype=hdt, pin_memory=True)
+        host_out = torch.empty(NPTS, dtype=hdt, pin_memory=True)
+        get(s.handle, host_in.data_ptr(), False)
         for _ in range(3):
-            P.gp.gp_set_psi_ptr(s.handle, host_in.data_ptr(), False)
+            put(s.handle, host_in.data_ptr(), False)
             s.step_imag(1)
-            P.gp.gp_get_psi_ptr(s.handle, host_out.data_ptr(), False)
+            get(s.handle, host_out.data_ptr(), False)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            P.gp.gp_set_psi_ptr(s.handle, host_in.data_ptr(), False)
+            put(s.handle, host_in.data_ptr(), False)
             s.step_imag(1)
-            P.gp.gp_get_psi_ptr(s.handle, host_out.data_ptr(), False)
+            get(s.handle, host_out.data_ptr(), False)
         torch.cuda.synchronize()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
+        name = "_f32" if f32 else ""
         e2e = {"value": round(world * NPTS * args.e2e_steps / e2e_s, 1), "unit": "grid-point-steps/s",
-               "h2d_bytes_per_step": NPTS * 8, "d2h_bytes_per_step": NPTS * 8,
+               "h2d_bytes_per_step": NPTS * sbytes, "d2h_bytes_per_step": NPTS * sbytes,
                "steps": args.e2e_steps,
-               "api": "gp_set_psi(pinned FP64 host field) + gp_step_imag(1) + gp_get_psi(pinned)"}
+               "api": f"gp_set_psi{name}(pinned host field) + gp_step_imag(1) + gp_get_psi{name}(pinned)"}
 
     # context: the same step back to back with L2 kept warm (no flush), one call
     torch.cuda.synchronize()

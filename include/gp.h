@@ -137,6 +137,17 @@ int gp_set_psi(gp_solver* s, const double* host, int is_complex);
  * GP_ERR_STATE.  Synchronises.                                                   */
 int gp_get_psi(gp_solver* s, double* host, int as_complex);
 
+/* FP32 host I/O for FP32 solvers (prec GP_F32): as gp_set_psi / gp_get_psi with
+ * float host buffers (nx*ny*nz floats, or 2*nx*ny*nz interleaved), one contiguous
+ * host copy each way with no FP64 conversion (rows are re-pitched on the device when
+ * the field's row pitch exceeds nx).
+ * gp_get_psi_f32 folds the pending renormalisation factor into the field first (the
+ * field is then stored normalised; nothing else changes).  as_complex must match the
+ * field (0: real, 1: complex), else GP_ERR_STATE; FP64 solvers return GP_ERR_ARG.
+ * gp_get_psi_f32 synchronises.                                                      */
+int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex);
+int gp_get_psi_f32(gp_solver* s, float* host, int as_complex);
+
 /* nsteps imaginary-time SSCN steps on the real field, each renormalised to unit
  * norm.  GP_ERR_STATE on a complex field.  Asynchronous.                         */
 int gp_step_imag(gp_solver* s, long nsteps);

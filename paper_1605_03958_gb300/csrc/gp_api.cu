@@ -1027,6 +1027,50 @@ int gp_get_psi(gp_solver* s, double* host, int as_complex) {
   return check_status(s);
 }
 
+int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex) {
+  if (!s || !host || (is_complex != 0 && is_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_set_psi");
+  s->is_complex = is_complex == 1;
+  const int m = is_complex;
+  const size_t eb = (size_t)4 * (m + 1), pitch = (size_t)s->L.pitch[m] * eb, row = (size_t)s->prm.nx * eb;
+  const size_t rows = (size_t)s->prm.ny * s->prm.nz;
+  if (pitch == row) {   // one contiguous host copy
+    GP_CUDA(s, cudaMemcpyAsync(s->field, host, rows * row, cudaMemcpyHostToDevice, s->stream));
+  } else {              // contiguous host copy to the staging area, pitched copy on the device
+    GP_CUDA(s, cudaMemcpyAsync(s->staging, host, rows * row, cudaMemcpyHostToDevice, s->stream));
+    GP_CUDA(s, cudaMemcpy2DAsync(s->field, pitch, s->staging, row, row, rows, cudaMemcpyDeviceToDevice,
+                                 s->stream));
+    GP_CUDA(s, cudaMemset2DAsync(static_cast<unsigned char*>(s->field) + row, pitch, 0, pitch - row, rows,
+                                 s->stream));   // pad columns stay zero
+  }
+  return set_scale_one(s);
+}
+
+int gp_get_psi_f32(gp_solver* s, float* host, int as_complex) {
+  if (!s || !host || (as_complex != 0 && as_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_get_psi");
+  if (as_complex != (s->is_complex ? 1 : 0))
+    return fail(s, GP_ERR_STATE, "as_complex must match the field (0: real, 1: complex)");
+  const int m = as_complex;
+  if (!s->is_complex) {   // fold the pending renormalisation factor into the field
+    const FieldParams f = field_params(s);
+    const cudaError_t e = gpk::launch_fold_scale<float>(f, false, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "fold");
+    const int rc = set_scale_one(s);
+    if (rc != GP_OK) return rc;
+  }
+  const size_t eb = (size_t)4 * (m + 1), pitch = (size_t)s->L.pitch[m] * eb, row = (size_t)s->prm.nx * eb;
+  const size_t rows = (size_t)s->prm.ny * s->prm.nz;
+  if (pitch == row) {
+    GP_CUDA(s, cudaMemcpyAsync(host, s->field, rows * row, cudaMemcpyDeviceToHost, s->stream));
+  } else {
+    GP_CUDA(s, cudaMemcpy2DAsync(s->staging, row, s->field, pitch, row, rows, cudaMemcpyDeviceToDevice,
+                                 s->stream));
+    GP_CUDA(s, cudaMemcpyAsync(host, s->staging, rows * row, cudaMemcpyDeviceToHost, s->stream));
+  }
+  return check_status(s);
+}
+
 int gp_step_imag(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
   if (s->is_complex) return fail(s, GP_ERR_STATE, "imaginary-time steps need a real field");

@@ -185,6 +185,9 @@ template <class R> cudaError_t launch_half_pointwise(const FieldParams& p, bool 
                                                      const void* fx, const void* fyz, double dtg,
                                                      bool apply_scale, bool norm, cudaStream_t st);
 template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaStream_t st);
+// psi <- *p.scale psi in place (the caller then sets the factor to 1).
+template <class R> cudaError_t launch_fold_scale(const FieldParams& p, bool complex_field,
+                                                 cudaStream_t st);
 template <class R> cudaError_t launch_init_gaussian(const FieldParams& p, double wx, double wy,
                                                     double wz, cudaStream_t st);
 template <class R> cudaError_t launch_import(const FieldParams& p, const double* src,

@@ -236,6 +236,22 @@ __global__ void __launch_bounds__(kReduceThreads) k_half_pointwise(const FieldPa
   }
 }
 
+// ------------------------------------------------- fold the pending factor
+
+template <class R, bool CPLX>
+__global__ void k_fold_scale(const FieldParams p) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  const R s = (R)(*p.scale);
+  E* psi = static_cast<E*>(p.psi);
+  const long long nrows = (long long)p.ny * p.nz;
+  for (long long r = blockIdx.x; r < nrows; r += gridDim.x)
+    for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
+      const size_t idx = (size_t)r * p.pitch + i;
+      psi[idx] = F::scaled(psi[idx], s);
+    }
+}
+
 // ------------------------------------------------------------ initial Gaussian
 
 template <class R>
@@ -395,6 +411,13 @@ cudaError_t launch_half_pointwise(const FieldParams& p, bool complex_field, cons
 }
 
 template <class R>
+cudaError_t launch_fold_scale(const FieldParams& p, bool complex_field, cudaStream_t st) {
+  if (complex_field) k_fold_scale<R, true><<<grid_for_rows(p), 256, 0, st>>>(p);
+  else k_fold_scale<R, false><<<grid_for_rows(p), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t launch_init_gaussian(const FieldParams& p, double wx, double wy, double wz,
                                  cudaStream_t st) {
   k_init_gaussian<R><<<grid_for_rows(p), 256, 0, st>>>(p, wx, wy, wz);
@@ -457,6 +480,7 @@ cudaError_t launch_cols_sum(const double* in, int rows, int cols, double w, doub
   template cudaError_t launch_norm_to_scale<R>(const FieldParams&, cudaStream_t);             \
   template cudaError_t launch_half_pointwise<R>(const FieldParams&, bool, const void*,       \
                                                 const void*, double, bool, bool, cudaStream_t); \
+  template cudaError_t launch_fold_scale<R>(const FieldParams&, bool, cudaStream_t);        \
   template cudaError_t launch_init_gaussian<R>(const FieldParams&, double, double, double,    \
                                                cudaStream_t);                                  \
   template cudaError_t launch_import<R>(const FieldParams&, const double*, bool, cudaStream_t); \

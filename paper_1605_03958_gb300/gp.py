@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_init_gaussian": (i, [vp, d, d, d]),
         "gp_set_psi": (i, [vp, vp, i]),
         "gp_get_psi": (i, [vp, vp, i]),
+        "gp_set_psi_f32": (i, [vp, vp, i]),
+        "gp_get_psi_f32": (i, [vp, vp, i]),
         "gp_step_imag": (i, [vp, l]),
         "gp_step_real": (i, [vp, l]),
         "gp_set_g": (i, [vp, d]),
@@ -194,6 +196,30 @@ def gp_get_psi(h, shape, as_complex: bool = False) -> np.ndarray:
 
 def gp_get_psi_ptr(h, host_ptr: int, as_complex: bool) -> None:
     _check(load_library().gp_get_psi(h, ctypes.c_void_p(host_ptr), int(as_complex)), h)
+
+
+def gp_set_psi_f32(h, host: np.ndarray) -> None:
+    """FP32 solvers: host float32 (real field) or complex64 (complex field), shape
+    (nz, ny, nx), copied straight into the device field."""
+    a = np.ascontiguousarray(host)
+    cplx = np.iscomplexobj(a)
+    a = a.astype(np.complex64 if cplx else np.float32, copy=False)
+    _check(load_library().gp_set_psi_f32(h, a.ctypes.data_as(ctypes.c_void_p), int(cplx)), h)
+
+
+def gp_get_psi_f32(h, shape, as_complex: bool = False) -> np.ndarray:
+    out = np.empty(shape, np.complex64 if as_complex else np.float32)
+    _check(load_library().gp_get_psi_f32(h, out.ctypes.data_as(ctypes.c_void_p), int(as_complex)), h)
+    return out
+
+
+def gp_set_psi_f32_ptr(h, host_ptr: int, is_complex: bool) -> None:
+    """gp_set_psi_f32 from a raw host address (e.g. a pinned torch float32 tensor)."""
+    _check(load_library().gp_set_psi_f32(h, ctypes.c_void_p(host_ptr), int(is_complex)), h)
+
+
+def gp_get_psi_f32_ptr(h, host_ptr: int, as_complex: bool) -> None:
+    _check(load_library().gp_get_psi_f32(h, ctypes.c_void_p(host_ptr), int(as_complex)), h)
 
 
 def gp_step_imag(h, nsteps: int) -> None:

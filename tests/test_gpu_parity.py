@@ -361,3 +361,35 @@ def test_fp32_truncated_kernels_match_tile_kernels_and_oracle(P, orc, shape, mod
     # each path within tol of the oracle, so any two within 2 tol of each other
     assert np.max(np.abs(outs["auto"][0] - outs["tile"][0])) <= 2 * tol
     assert np.max(np.abs(outs["stream"][0] - outs["tile"][0])) <= 2 * tol
+
+
+# ------------------------------------------------------------- FP32 host I/O
+
+@pytest.mark.parametrize("mode", ["imag", "real"])
+def test_fp32_host_io_matches_fp64_host_io(P, orc, mode):
+    """gp_set_psi_f32 / gp_get_psi_f32 (pitched copies, no staging) against the FP64
+    host I/O: an FP32-representable field goes in bit for bit, the same steps follow,
+    and the read-back equals the FP64 read-back rounded to FP32 (the pending factor
+    folded in first)."""
+    p = problem(orc, 37, 29, 23, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=80.0)
+    rng = np.random.default_rng(12)
+    psi = orc.init_gaussian(p).astype(np.float32)
+    if mode == "real":
+        psi = (psi * np.exp(0.3j * rng.standard_normal(p.shape))).astype(np.complex64)
+    a, b = solver(P, p, prec="f32"), solver(P, p, prec="f32")
+    P.gp.gp_set_psi_f32(a.handle, psi)
+    b.set_psi(psi.astype(np.complex128 if mode == "real" else np.float64))
+    cplx = mode == "real"
+    assert np.array_equal(P.gp.gp_get_psi_f32(a.handle, p.shape, cplx), psi)
+    for s in (a, b):
+        s.step_imag(7) if mode == "imag" else s.step_real(7)
+    x = P.gp.gp_get_psi_f32(a.handle, p.shape, cplx)
+    y = b.get_psi(as_complex=cplx)
+    assert np.max(np.abs(x - y)) <= 2e-7 * np.max(np.abs(y))
+    with pytest.raises(P.GPError):
+        P.gp.gp_get_psi_f32(a.handle, p.shape, not cplx)
+    f64 = solver(P, p, prec="f64")
+    with pytest.raises(P.GPError):
+        P.gp.gp_set_psi_f32(f64.handle, psi)
+    for s in (a, b, f64):
+        s.close()
