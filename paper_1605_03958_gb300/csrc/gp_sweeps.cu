@@ -857,9 +857,11 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
     for (int t = lane; t < 15 * rows; t += 32) {
       const int r = t / 15, k = t - 15 * r;
       E* row = slot_of(st, r);
-      if (k < 7) row[-2 - k] = F::scaled(row[k], R(-1));
-      else if (k < 14) row[nx + 1 + (k - 7)] = F::scaled(row[nx - 1 - (k - 7)], R(-1));
-      else row[nx] = F::zero();
+      // k < 7: -row[k] -> -2-k; k < 14: -row[nx-1-m] -> nx+1+m; k = 14: -row[-1] (= 0)
+      // -> nx, the ghost (a signed zero, which leaves every sum unchanged)
+      const int src = k < 7 ? k : k < 14 ? nx - 1 - (k - 7) : -1;
+      const int dst = k < 7 ? -2 - k : k < 14 ? nx + 1 + (k - 7) : nx;
+      row[dst] = F::scaled(row[src], R(-1));
     }
     __syncwarp();
     for (int idx = lane; idx < nv; idx += 32) {
@@ -975,14 +977,13 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
       if (act) *vp = raw;
     }
     __syncwarp();
-    // odd images about -1 (positions -2..-8) and about nx (nx+1..nx+7), ghost nx
-    if (lane < 7) {
-      row[-2 - lane] = F::scaled(row[lane], R(-1));
-    } else if (lane < 14) {
-      const int m = lane - 7;
-      row[nx + 1 + m] = F::scaled(row[nx - 1 - m], R(-1));
-    } else if (lane == 14) {
-      row[nx] = F::zero();
+    // odd images about -1 (positions -2..-8) and about nx (nx+1..nx+7), and the ghost
+    // nx as -row[-1] (a signed zero, which leaves every sum unchanged): one predicated
+    // load / negate / store per lane
+    if (lane < 15) {
+      const int src = lane < 7 ? lane : lane < 14 ? nx - 1 - (lane - 7) : -1;
+      const int dst = lane < 7 ? -2 - lane : lane < 14 ? nx + 1 + (lane - 7) : nx;
+      row[dst] = F::scaled(row[src], R(-1));
     }
     __syncwarp();
     E* grow = field + (size_t)(row0 + i) * pitch;
