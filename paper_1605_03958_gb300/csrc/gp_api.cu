@@ -407,6 +407,7 @@ void fill_sweep_params(gp_solver* s) {
       q.vz = vt + (size_t)(p.nx + p.ny) * rb;
       q.dt = p.dt;
       q.g = s->g;
+      q.band_dtg = (float)(p.dt * s->g);
       q.pw = 1;
       q.scale = s->scale;
       q.partials = s->partials;
@@ -1099,7 +1100,10 @@ int gp_set_g(gp_solver* s, double g) {
   if (!std::isfinite(g)) return fail(s, GP_ERR_ARG, "g must be finite");
   s->g = g;
   for (int m = 0; m < 2; ++m)
-    for (int a = 0; a < 3; ++a) s->sp[m][a].g = g;
+    for (int a = 0; a < 3; ++a) {
+      s->sp[m][a].g = g;
+      s->sp[m][a].band_dtg = (float)(s->sp[m][a].dt * g);
+    }
   return GP_OK;
 }
 

@@ -67,6 +67,7 @@ struct SweepParams {
   int band_stages;       // x: groups of rows in flight per warp
   int band_group;        // x: rows per group (worked on together by the warp's lanes)
   int band_seg;          // y / z: points per line segment (a multiple of 2 band_w + 1)
+  float band_dtg;        // x: dt g in FP32
   // pointwise substep (x sweep only)
   int pw;                // 1: pointwise substep fused on load; 0: kinetic-only step
   const void* vx;

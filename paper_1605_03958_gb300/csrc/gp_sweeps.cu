@@ -369,9 +369,19 @@ constexpr int kStreamU = GP_STREAM_U;  // chunk length of the streaming kernel (
 constexpr int kHeadMax = 8;     // largest `head` the streaming kernel handles
 
 // Fixed-order block reduction of one FP64 value per warp into partials[block];
-// the last block to finish sums the partials (all its threads, loads issued ahead,
-// a fixed-order tree) and writes the renormalisation factor.  Every thread of the
-// block must call it.
+// the last block to finish sums the partials and writes the renormalisation factor.
+// Every thread of the block must call it.  The last block's work is the kernel's
+// tail (FP64 is narrow on this part: every dependent FP64 operation costs about a
+// warp's worth of pipe cycles), so its sums are shallow pairwise trees in a fixed
+// order: four partials per thread loaded together, (x0 + x1) + (x2 + x3), the warp
+// shuffle tree, the warps' sums pairwise; the factor is rsqrt(norm), like
+// 1 / sqrt(norm) within 1 ulp of the exact value.
+__device__ __forceinline__ double sum_fixed(const double* w, int n) {
+  if (n == 4) return (w[0] + w[1]) + (w[2] + w[3]);
+  double v = w[0];
+  for (int i = 1; i < n; ++i) v += w[i];
+  return v;
+}
 __device__ __forceinline__ void norm_finish(double acc, double* partials, unsigned int* counter,
                                             unsigned int nb, unsigned int bid, double* scale_out,
                                             int* status, double dV) {
@@ -382,46 +392,35 @@ __device__ __forceinline__ void norm_finish(double acc, double* partials, unsign
   if (lane == 0) wpart[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < nw; ++w) v += wpart[w];
-    partials[bid] = v;
+    partials[bid] = sum_fixed(wpart, nw);
     __threadfence();
     last = (atomicAdd(counter, 1u) == nb - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // thread t sums partials t, t + blockDim, ... (8 loads in flight), then a tree
   const unsigned int T = blockDim.x;
-  double s = 0.0, c = 0.0;
-  for (unsigned int t0 = threadIdx.x; t0 < nb; t0 += 8 * T) {
-    double x[8];
+  auto quad = [&](unsigned int t0) {
+    double x[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 4; ++q) {
       const unsigned int t = t0 + q * T;
       x[q] = t < nb ? __ldcg(partials + t) : 0.0;
     }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double u = s + x[q];
-      c += (fabs(s) >= fabs(x[q])) ? (s - u) + x[q] : (x[q] - u) + s;
-      s = u;
-    }
-  }
-  s += c;
+    return (x[0] + x[1]) + (x[2] + x[3]);
+  };
+  double s = quad(threadIdx.x);
+  for (unsigned int t0 = threadIdx.x + 4 * T; t0 < nb; t0 += 4 * T) s += quad(t0);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) wpart[warp] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < nw; ++w) tot += wpart[w];
-    const double norm = tot * dV;
+    const double norm = sum_fixed(wpart, nw) * dV;
     if (!(norm > 0.0) || !isfinite(norm)) atomicOr(status, kStatusNonFinite);
-    *scale_out = 1.0 / sqrt(norm);
+    *scale_out = rsqrt(norm);
     *counter = 0u;
   }
 }
-
 __device__ __forceinline__ void norm_block_finish(double acc, const SweepParams& p) {
   norm_finish(acc, p.partials, p.counter, gridDim.x, blockIdx.x, p.scale_out, p.status, p.dV);
 }
@@ -780,7 +779,9 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
   const int ngroups = (nrow + G - 1) / G;
   const long long row0 = a.row0;
   E* field = a.field;
-  const E* wt = a.wt;
+  E wt[W + 1];   // wt[0] = w_0 - 1, wt[k] = w_k
+#pragma unroll
+  for (int k = 0; k <= W; ++k) wt[k] = a.wt[W + k];
   const float4* fx = a.fx;
   const E* fyz = a.fyz;
   const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
@@ -788,8 +789,7 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
   const R dtg = (R)a.dtg;
   // row slot r of stage st
   auto slot_of = [&](int st, int r) { return slots + (size_t)(st * G + r) * se; };
-  auto issue = [&](int i) {   // group i of this warp -> stage i % S, one bulk copy per row
-    const int st = i % S;
+  auto issue = [&](int i, int st) {   // group i of this warp -> stage st = i mod S, one bulk copy per row
     const int rows = min(G, nrow - i * G);
     mbar_arrive_expect_tx(&full[st], (uint32_t)rows * rowbytes);
     for (int r = 0; r < rows; ++r)
@@ -797,18 +797,19 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
                 &full[st]);
   };
   if (lane == 0)
-    for (int i = 0; i < S && i < ngroups; ++i) issue(i);
+    for (int i = 0; i < S && i < ngroups; ++i) issue(i, i);
   // trap factor of row `lane` of the current group, loaded one group ahead; a lane
   // takes its row's factor from lane r by shuffle
   E fcur = lane < min(G, nrow) ? fyz[row0 + lane] : F::zero();
 
+  int st = 0;
+  uint32_t phase = 0;
   for (int i = 0; i < ngroups; ++i) {
-    const int st = i % S;
     const int rows = min(G, nrow - i * G);
     const int nv = rows * nvec;            // vectors of the group
     const long long gr0 = row0 + (long long)i * G;
     const E fnext = (i + 1 < ngroups && lane < min(G, nrow - (i + 1) * G)) ? fyz[gr0 + G + lane] : F::zero();
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)(i / S) & 1u, kWaitLimitNs))) {
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], phase, kWaitLimitNs))) {
       if (lane == 0) {
         atomicOr(a.status, kStatusTimeout);
         // wait (bounded) for every copy still in flight before the warp exits
@@ -878,9 +879,9 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
         const int c = H * EPT + e;   // the output's position in the window
-        E acc = F::mul(wt[W], win[c]);
+        E acc = F::mul(wt[0], win[c]);
 #pragma unroll
-        for (int k = 1; k <= W; ++k) acc = F::chain(wt[W + k], F::add(win[c - k], win[c + k]), acc);
+        for (int k = 1; k <= W; ++k) acc = F::chain(wt[k], F::add(win[c - k], win[c + k]), acc);
         o[e] = F::add(win[c], acc);
       }
       E* grow = field + (size_t)(gr0 + r) * pitch;
@@ -895,13 +896,21 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
     __syncwarp();
     if (lane == 0 && i + S < ngroups) {
       fence_smem_to_async();
-      issue(i + S);
+      issue(i + S, st);
     }
     fcur = fnext;
+    if (++st == S) {
+      st = 0;
+      phase ^= 1u;
+    }
   }
 }
 
 // One row at a time (rows of 32 or more 16-byte vectors fill the lanes by themselves).
+// Per-row work is kept to the copy, the wait and the images: the stage and its phase
+// advance by counting, the trap factors along x of the lane's first NC vectors stay
+// in registers (they are the same in every row), the band weights too, and the first
+// NC passes over a row are unrolled.
 template <class R, bool CPLX, int W>
 __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R, CPLX>::E>& a,
                                             uint64_t* full, typename Field<R, CPLX>::E* slots) {
@@ -910,34 +919,95 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
   constexpr int EPT = 16 / (int)sizeof(E);   // elements per 16-byte vector
   constexpr int H = (W + EPT - 1) / EPT;     // halo vectors on each side of a window
   constexpr int NV = 2 * H + 1;              // vectors in a window
+  constexpr int NC = 2;                      // 32-lane passes with cached trap factors
   static_assert(H * EPT <= kBandPad, "window inside the slot");
-  const int nx = a.nx, pitch = a.pitch, S = a.S, nrow = a.nrow;
+  const int nx = a.nx, pitch = a.pitch, S = a.S, nrow = a.nrow, se = a.slot_elems;
   const int lane = threadIdx.x & 31;
   const int nvec = (nx + EPT - 1) / EPT;
-  const long long row0 = a.row0;
   E* field = a.field;
-  const E* wt = a.wt;
   const float4* fx = a.fx;
-  const E* fyz = a.fyz;
   const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
+  E* gsrc = field + (size_t)a.row0 * pitch;   // row i + S's copy source
+  if (lane == 0)
+    for (int i = 0; i < S && i < nrow; ++i) {
+      mbar_arrive_expect_tx(&full[i], rowbytes);
+      bulk_load(slots + (size_t)i * se, gsrc, rowbytes, &full[i]);
+      gsrc += pitch;
+    }
+  E wt[W + 1];   // wt[0] = w_0 - 1, wt[k] = w_k
+#pragma unroll
+  for (int k = 0; k <= W; ++k) wt[k] = a.wt[W + k];
+  float4 fxc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    fxc[c] = lane + 32 * c < nvec ? __ldg(fx + lane + 32 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
   const R s = (R)(*a.scale);
   const R dtg = (R)a.dtg;
-  auto issue = [&](int i) {   // row i of this warp -> stage i % S
-    const int st = i % S;
-    mbar_arrive_expect_tx(&full[st], rowbytes);
-    bulk_load(slots + (size_t)st * a.slot_elems, field + (size_t)(row0 + i) * pitch, rowbytes,
-              &full[st]);
+  const bool pw = a.pw != 0;
+  const E* fyz = a.fyz + a.row0;
+  E f_next = fyz[0];
+  E* grow = field + (size_t)a.row0 * pitch;   // row i's output
+  int st = 0;
+  uint32_t phase = 0;
+
+  // pointwise substep of vector v (lanes past the row idle but vote)
+  auto point = [&](E* row, int v, float4 fxv, E fr) {
+    const bool act = v < nvec;
+    float4* vp = reinterpret_cast<float4*>(row + (act ? v : 0) * EPT);
+    float4 raw = *vp;
+    E* ev = reinterpret_cast<E*>(&raw);
+    const E* fe = reinterpret_cast<const E*>(&fxv);
+    R y[EPT];
+    R ymax = R(0);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      ev[e] = F::scaled(ev[e], s);
+      y[e] = dtg * F::abs2(ev[e]);
+      ymax = fmaxf(ymax, fabsf(y[e]));
+    }
+    if (!pw) {
+      // kinetic-only step: the pending factor alone
+    } else if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_small(ev[e], F::mul(fe[e], fr), y[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_full(ev[e], F::mul(fe[e], fr), y[e]);
+    }
+    if (act) *vp = raw;
   };
-  if (lane == 0)
-    for (int i = 0; i < S && i < nrow; ++i) issue(i);
-  E f_next = fyz[row0];
+  // banded operator at vector v of the row, stored to the field
+  auto band = [&](const E* row, int v) {
+    const int x0 = v * EPT;
+    const float4* src = reinterpret_cast<const float4*>(row + x0 - H * EPT);
+    float4 wv[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) wv[q] = src[q];
+    const E* win = reinterpret_cast<const E*>(wv);
+    float4 ov;
+    E* o = reinterpret_cast<E*>(&ov);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int c = H * EPT + e;   // the output's position in the window
+      E acc = F::mul(wt[0], win[c]);
+#pragma unroll
+      for (int k = 1; k <= W; ++k) acc = F::chain(wt[k], F::add(win[c - k], win[c + k]), acc);
+      o[e] = F::add(win[c], acc);
+    }
+    if (x0 + EPT <= nx) {
+      *reinterpret_cast<float4*>(grow + x0) = ov;
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e)
+        if (x0 + e < nx) grow[x0 + e] = o[e];
+    }
+  };
 
   for (int i = 0; i < nrow; ++i) {
-    const int st = i % S;
-    E* row = slots + (size_t)st * a.slot_elems;
+    E* row = slots + (size_t)st * se;
     const E fr = f_next;
-    if (i + 1 < nrow) f_next = fyz[row0 + i + 1];
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)(i / S) & 1u, kWaitLimitNs))) {
+    if (i + 1 < nrow) f_next = fyz[i + 1];
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], phase, kWaitLimitNs))) {
       if (lane == 0) {
         atomicOr(a.status, kStatusTimeout);
         // wait (bounded) for every copy still in flight before the warp exits
@@ -949,33 +1019,11 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
     }
     // pointwise substep in place (past nx too: overwritten below); the lanes of a
     // warp take the polynomial branch together when every argument allows it
-    for (int v0 = 0; v0 < nvec; v0 += 32) {
-      const int v = v0 + lane;
-      const bool act = v < nvec;
-      float4* vp = reinterpret_cast<float4*>(row + (act ? v : 0) * EPT);
-      float4 raw = *vp;
-      const float4 fxv = __ldg(fx + (act ? v : 0));
-      E* ev = reinterpret_cast<E*>(&raw);
-      const E* fe = reinterpret_cast<const E*>(&fxv);
-      R y[EPT];
-      R ymax = R(0);
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        ev[e] = F::scaled(ev[e], s);
-        y[e] = dtg * F::abs2(ev[e]);
-        ymax = fmaxf(ymax, fabsf(y[e]));
-      }
-      if (!a.pw) {
-        // kinetic-only step: the pending factor alone
-      } else if (__all_sync(0xffffffffu, !act || ymax <= R(0.0625))) {
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_small(ev[e], F::mul(fe[e], fr), y[e]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) ev[e] = F::nonlinear_full(ev[e], F::mul(fe[e], fr), y[e]);
-      }
-      if (act) *vp = raw;
-    }
+    for (int c = 0; c < NC; ++c)
+      if (32 * c < nvec) point(row, lane + 32 * c, fxc[c], fr);
+    for (int v0 = 32 * NC; v0 < nvec; v0 += 32)
+      point(row, v0 + lane, __ldg(fx + min(v0 + lane, nvec - 1)), fr);
     __syncwarp();
     // odd images about -1 (positions -2..-8) and about nx (nx+1..nx+7), and the ghost
     // nx as -row[-1] (a signed zero, which leaves every sum unchanged): one predicated
@@ -986,36 +1034,21 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
       row[dst] = F::scaled(row[src], R(-1));
     }
     __syncwarp();
-    E* grow = field + (size_t)(row0 + i) * pitch;
-    for (int v = lane; v < nvec; v += 32) {
-      const int x0 = v * EPT;
-      const float4* src = reinterpret_cast<const float4*>(row + x0 - H * EPT);
-      float4 wv[NV];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) wv[q] = src[q];
-      const E* win = reinterpret_cast<const E*>(wv);
-      float4 ov;
-      E* o = reinterpret_cast<E*>(&ov);
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int c = H * EPT + e;   // the output's position in the window
-        E acc = F::mul(wt[W], win[c]);
-#pragma unroll
-        for (int k = 1; k <= W; ++k) acc = F::chain(wt[W + k], F::add(win[c - k], win[c + k]), acc);
-        o[e] = F::add(win[c], acc);
-      }
-      if (x0 + EPT <= nx) {
-        *reinterpret_cast<float4*>(grow + x0) = ov;
-      } else {
-#pragma unroll
-        for (int e = 0; e < EPT; ++e)
-          if (x0 + e < nx) grow[x0 + e] = o[e];
-      }
-    }
+    for (int c = 0; c < NC; ++c)
+      if (lane + 32 * c < nvec) band(row, lane + 32 * c);
+    for (int v = lane + 32 * NC; v < nvec; v += 32) band(row, v);
     __syncwarp();
     if (lane == 0 && i + S < nrow) {
       fence_smem_to_async();
-      issue(i + S);
+      mbar_arrive_expect_tx(&full[st], rowbytes);
+      bulk_load(row, gsrc, rowbytes, &full[st]);
+      gsrc += pitch;
+    }
+    grow += pitch;
+    if (++st == S) {
+      st = 0;
+      phase ^= 1u;
     }
   }
 }
@@ -1049,7 +1082,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.G = G;
   a.slot_elems = slot_elems;
   a.pw = p.pw;
-  a.dtg = (float)(p.dt * p.g);
+  a.dtg = p.band_dtg;
   if (GROUPED) x_band_rows<R, CPLX, W>(a, full, slots);
   else x_band_rows_single<R, CPLX, W>(a, full, slots);
 }
