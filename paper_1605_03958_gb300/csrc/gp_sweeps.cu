@@ -393,12 +393,15 @@ __device__ __forceinline__ void norm_finish(double acc, double* partials, unsign
   __syncthreads();
   if (threadIdx.x == 0) {
     partials[bid] = sum_fixed(wpart, nw);
-    __threadfence();
-    last = (atomicAdd(counter, 1u) == nb - 1);
+    // release of this block's partial and, for the last block, acquire of all the
+    // others' (the counter's atomic updates form one release sequence); the block's
+    // barrier then orders its threads' loads after the acquire
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(counter) : "memory");
+    last = (old == nb - 1);
   }
   __syncthreads();
   if (!last) return;
-  __threadfence();
   const unsigned int T = blockDim.x;
   auto quad = [&](unsigned int t0) {
     double x[4];
