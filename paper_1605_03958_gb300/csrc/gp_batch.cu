@@ -401,7 +401,7 @@ int rebuild(gp_pool* P) {
     for (int i = 0; i < ns; ++i)
       if (P->slots[i].live && P->slots[i].mode == m)
         rows_tot += (long long)P->slots[i].prm.ny * P->slots[i].prm.nz;
-    const long long cap = (long long)P->nsm * bps * gpk::kBandWarps;
+    const long long cap = (long long)P->nsm * bps * gpk::kBatchXWarps;
     const int rpw = (int)std::max<long long>(1, (rows_tot + cap - 1) / cap);
     std::vector<XItem> xi;
     std::vector<LineBlock> lb[3];
@@ -465,7 +465,7 @@ int launch_step(gp_pool* P) {
       b.group_max = P->x_group_max[m];
       b.slot_elems = P->slot_elems[m];
       b.status = P->d_status;
-      const int grid = a == 0 ? (b.nitems + gpk::kBandWarps - 1) / gpk::kBandWarps : b.nitems;
+      const int grid = a == 0 ? (b.nitems + gpk::kBatchXWarps - 1) / gpk::kBatchXWarps : b.nitems;
       const cudaError_t e = gpk::launch_batch_sweep(a, P->wl[m][a], b, m == 1, grid,
                                                     a == 0 ? P->x_smem[m] : 0, P->stream);
       if (e != cudaSuccess) return pcuda(P, e, "batched sweep launch");

@@ -24,8 +24,11 @@ constexpr int kMaxExtent = 2048;
 // Longest line segment one TMA box covers (hardware limit on a box dimension).
 constexpr int kMaxBox = 256;
 
-// Warps per block of the banded FP32 x sweep (each warp works on its own rows).
-constexpr int kBandWarps = 4;
+// Warps per block of the banded FP32 x sweep (each warp works on its own rows): few
+// large blocks fill the SMs sooner than many small ones when the sweep starts.
+constexpr int kBandWarps = 12;
+// Warps per block of the batched x sweep (one work item per warp).
+constexpr int kBatchXWarps = 4;
 // Largest half-width of the banded operators (weights arrays hold 2 kBandHalfMax + 1).
 constexpr int kBandHalfMax = 8;
 

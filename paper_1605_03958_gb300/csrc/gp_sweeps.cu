@@ -1092,16 +1092,16 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
 
 // Batched x sweep: warp w of the launch takes work item w (rows of one slot).
 template <class R, bool CPLX, int W>
-__global__ void __launch_bounds__(32 * kBandWarps) k_batch_x_band(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(32 * kBatchXWarps) k_batch_x_band(const __grid_constant__ BatchArgs b) {
   using E = typename Field<R, CPLX>::E;
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = b.stages, GM = b.group_max, slot_elems = b.slot_elems;
   const int wib = threadIdx.x >> 5;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
-  const int w = blockIdx.x * kBandWarps + wib;
+  const int w = blockIdx.x * kBatchXWarps + wib;
   // the item's G rows of a stage sit in its first G of the GM slots per stage
   const int G = w < b.nitems ? static_cast<const XItem*>(b.items)[w].group : 1;
-  E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * GM * slot_elems + kBandPad;
+  E* slots = reinterpret_cast<E*>(smem + 128 * kBatchXWarps) + (size_t)wib * S * GM * slot_elems + kBandPad;
   x_band_init(full, slots, S, S * G, slot_elems);
   pdl_begin();
   if (w >= b.nitems) return;
@@ -1449,15 +1449,15 @@ cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_
 }
 
 size_t batch_x_smem(int stages, int group_max, int slot_elems, bool complex_field) {
-  return 128 * kBandWarps +
-         (size_t)kBandWarps * stages * group_max * slot_elems * (complex_field ? 8 : 4);
+  return 128 * kBatchXWarps +
+         (size_t)kBatchXWarps * stages * group_max * slot_elems * (complex_field ? 8 : 4);
 }
 
 template <int W> static cudaError_t batch_prepare_W(bool cplx, size_t x_smem, int* bps) {
   void (*k)(BatchArgs) = cplx ? k_batch_x_band<float, true, W> : k_batch_x_band<float, false, W>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x_smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, 32 * kBandWarps, x_smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, 32 * kBatchXWarps, x_smem);
 }
 
 cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_blocks_per_sm) {
@@ -1473,8 +1473,8 @@ template <int W>
 static cudaError_t launch_batch_W(int axis, const BatchArgs& b, bool cplx, int grid, size_t smem,
                                   cudaStream_t st) {
   if (axis == 0)
-    return cplx ? launch_pdl(k_batch_x_band<float, true, W>, grid, 32 * kBandWarps, smem, st, b)
-                : launch_pdl(k_batch_x_band<float, false, W>, grid, 32 * kBandWarps, smem, st, b);
+    return cplx ? launch_pdl(k_batch_x_band<float, true, W>, grid, 32 * kBatchXWarps, smem, st, b)
+                : launch_pdl(k_batch_x_band<float, false, W>, grid, 32 * kBatchXWarps, smem, st, b);
   if (axis == 1)
     return cplx ? launch_pdl(k_batch_band_line<float, true, 1, false, W>, grid, 128, 0, st, b)
                 : launch_pdl(k_batch_band_line<float, false, 1, false, W>, grid, 128, 0, st, b);
