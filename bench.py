@@ -401,10 +401,13 @@ def cpu_baseline():
     t1 = _oracle_sample(NZ, 1, threads)
     steps = max(1, min(100, int(20.0 / max(t1, 1e-3))))
     t = _oracle_sample(NZ, steps, threads)
+    ts = _oracle_sample(NZ, 1, 1)
     return {"value": round(NPTS * steps / t, 1), "unit": "grid-point-steps/s", "cores": threads,
             "kind": "oracle",
             "sample": f"{steps} FP64 imaginary-time steps of the full 240x200x160 grid, "
-                      f"OpenMP over line solves on {threads} threads"}
+                      f"OpenMP over line solves on {threads} threads",
+            "single_thread": {"value": round(NPTS / ts, 1), "unit": "grid-point-steps/s",
+                              "cores": 1, "sample": "1 FP64 imaginary-time step of the full grid"}}
 
 
 def run_reference(args):
