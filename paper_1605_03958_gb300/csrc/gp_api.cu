@@ -302,6 +302,10 @@ struct gp_solver {
   float band_wt[2][3][2 * 17] = {};  // its weights (complex: pairs)
   int nsm = 0;
   CUtensorMap tmap[2][3];  // [mode][axis]; axis 0 unused (64-byte aligned type)
+  // one Lie step as a CUDA graph per mode, captured on first use on cap_stream
+  cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;
+  bool step_graph = true;            // false once capture failed: direct launches only
   // timing
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -808,9 +812,11 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
   return GP_OK;
 }
 
-template <class R> int lie_steps(gp_solver* s, long nsteps) {
+// One Lie step launched directly: the three sweeps (2D: x, y, the staging copy and
+// the norm pass).
+template <class R> int lie_step_direct(gp_solver* s) {
   const bool two_d = s->prm.nz == 1;
-  for (long t = 0; t < nsteps; ++t)
+  {
     for (int a = 0; a < 3; ++a) {
       if (a == 2 && two_d) {
         // 2D: no z sweep.  A fast y sweep wrote the staging area: copy it back; then
@@ -831,6 +837,64 @@ template <class R> int lie_steps(gp_solver* s, long nsteps) {
       const int rc = run_sweep<R>(s, a);
       if (rc != GP_OK) return rc;
     }
+  }
+  return GP_OK;
+}
+
+void drop_step_graphs(gp_solver* s) {
+  for (auto& e : s->step_exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+}
+
+// Capture one Lie step of mode m on the side stream into s->step_exec[m]; on any
+// failure the solver falls back to direct launches for good.
+template <class R> void capture_step(gp_solver* s, int m) {
+  if (!s->cap_stream &&
+      cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s->cap_stream = nullptr;
+    s->step_graph = false;
+    return;
+  }
+  const cudaStream_t orig = s->stream;
+  const std::string saved_err = s->err;
+  s->stream = s->cap_stream;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  const int rc = ok ? lie_step_direct<R>(s) : GP_OK;
+  if (ok) ok = cudaStreamEndCapture(s->cap_stream, &g) == cudaSuccess && rc == GP_OK;
+  s->stream = orig;
+  if (ok) ok = cudaGraphInstantiate(&s->step_exec[m], g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    s->step_exec[m] = nullptr;
+    s->step_graph = false;
+    s->err = saved_err;
+  }
+}
+
+// nsteps Lie steps.  A single step (the usual call between reads of the state)
+// replays the step's graph: one submission instead of separate launches starts the
+// step about 2 us sooner.  Longer runs launch directly, so that each step's first
+// sweep overlaps the previous step's last through programmatic dependent launch
+// (graphs replayed back to back would serialise there).  The graph holds the sweep
+// parameters by value: gp_set_g drops it.
+template <class R> int lie_steps(gp_solver* s, long nsteps) {
+  if (nsteps == 1 && s->step_graph && !s->timing && !s->kinetic_only) {
+    const int m = s->is_complex ? 1 : 0;
+    if (!s->step_exec[m]) capture_step<R>(s, m);
+    if (s->step_exec[m]) {
+      GP_CUDA(s, cudaGraphLaunch(s->step_exec[m], s->stream));
+      return GP_OK;
+    }
+  }
+  for (long t = 0; t < nsteps; ++t) {
+    const int rc = lie_step_direct<R>(s);
+    if (rc != GP_OK) return rc;
+  }
   return GP_OK;
 }
 
@@ -979,6 +1043,8 @@ void gp_destroy(gp_solver* s) {
     cudaEventDestroy(t.stop);
   }
   for (auto ev : s->pool) cudaEventDestroy(ev);
+  drop_step_graphs(s);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->owns && s->base) cudaFree(s->base);
   delete s;
 }
@@ -1104,6 +1170,7 @@ int gp_set_g(gp_solver* s, double g) {
       s->sp[m][a].g = g;
       s->sp[m][a].band_dtg = (float)(s->sp[m][a].dt * g);
     }
+  drop_step_graphs(s);   // they hold the old parameters
   return GP_OK;
 }
 
