@@ -302,8 +302,9 @@ struct gp_solver {
   float band_wt[2][3][2 * 17] = {};  // its weights (complex: pairs)
   int nsm = 0;
   CUtensorMap tmap[2][3];  // [mode][axis]; axis 0 unused (64-byte aligned type)
-  // one Lie step as a CUDA graph per mode, captured on first use on cap_stream
+  // one Lie / Strang step as a CUDA graph per mode, captured on first use on cap_stream
   cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+  cudaGraphExec_t strang_exec[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
   bool step_graph = true;            // false once capture failed: direct launches only
   // timing
@@ -842,15 +843,16 @@ template <class R> int lie_step_direct(gp_solver* s) {
 }
 
 void drop_step_graphs(gp_solver* s) {
-  for (auto& e : s->step_exec) {
-    if (e) cudaGraphExecDestroy(e);
-    e = nullptr;
-  }
+  for (auto* set : {s->step_exec, s->strang_exec})
+    for (int m = 0; m < 2; ++m) {
+      if (set[m]) cudaGraphExecDestroy(set[m]);
+      set[m] = nullptr;
+    }
 }
 
-// Capture one Lie step of mode m on the side stream into s->step_exec[m]; on any
+// Capture the launches fn makes on s->stream into *exec, on the side stream; on any
 // failure the solver falls back to direct launches for good.
-template <class R> void capture_step(gp_solver* s, int m) {
+template <class Fn> void capture_graph(gp_solver* s, cudaGraphExec_t* exec, Fn fn) {
   if (!s->cap_stream &&
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -863,14 +865,14 @@ template <class R> void capture_step(gp_solver* s, int m) {
   s->stream = s->cap_stream;
   cudaGraph_t g = nullptr;
   bool ok = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  const int rc = ok ? lie_step_direct<R>(s) : GP_OK;
+  const int rc = ok ? fn() : GP_OK;
   if (ok) ok = cudaStreamEndCapture(s->cap_stream, &g) == cudaSuccess && rc == GP_OK;
   s->stream = orig;
-  if (ok) ok = cudaGraphInstantiate(&s->step_exec[m], g, 0) == cudaSuccess;
+  if (ok) ok = cudaGraphInstantiate(exec, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
   if (!ok) {
     cudaGetLastError();
-    s->step_exec[m] = nullptr;
+    *exec = nullptr;
     s->step_graph = false;
     s->err = saved_err;
   }
@@ -885,7 +887,7 @@ template <class R> void capture_step(gp_solver* s, int m) {
 template <class R> int lie_steps(gp_solver* s, long nsteps) {
   if (nsteps == 1 && s->step_graph && !s->timing && !s->kinetic_only) {
     const int m = s->is_complex ? 1 : 0;
-    if (!s->step_exec[m]) capture_step<R>(s, m);
+    if (!s->step_exec[m]) capture_graph(s, &s->step_exec[m], [s] { return lie_step_direct<R>(s); });
     if (s->step_exec[m]) {
       GP_CUDA(s, cudaGraphLaunch(s->step_exec[m], s->stream));
       return GP_OK;
@@ -928,7 +930,7 @@ template <class R> int half_pointwise(gp_solver* s, bool apply_scale, bool norm)
 // Real time: |psi| is invariant under the pointwise phase, so P(dt/2) P(dt/2) = P(dt)
 // and n steps are P(dt/2), K, n-1 fused Lie steps, P(dt/2).  Imaginary time: each
 // step is P(dt/2) (pending factor applied), K, P(dt/2) with its norm.
-template <class R> int strang_steps(gp_solver* s, long nsteps) {
+template <class R> int strang_steps_direct(gp_solver* s, long nsteps) {
   if (nsteps == 0) return GP_OK;
   int rc;
   if (s->is_complex) {
@@ -943,6 +945,20 @@ template <class R> int strang_steps(gp_solver* s, long nsteps) {
     if ((rc = half_pointwise<R>(s, false, true)) != GP_OK) return rc;
   }
   return GP_OK;
+}
+
+// A single Strang step replays its graph, like a single Lie step.
+template <class R> int strang_steps(gp_solver* s, long nsteps) {
+  if (nsteps == 1 && s->step_graph && !s->timing) {
+    const int m = s->is_complex ? 1 : 0;
+    if (!s->strang_exec[m])
+      capture_graph(s, &s->strang_exec[m], [s] { return strang_steps_direct<R>(s, 1); });
+    if (s->strang_exec[m]) {
+      GP_CUDA(s, cudaGraphLaunch(s->strang_exec[m], s->stream));
+      return GP_OK;
+    }
+  }
+  return strang_steps_direct<R>(s, nsteps);
 }
 
 template <class R> int steps(gp_solver* s, long nsteps) {

@@ -84,3 +84,20 @@ def test_timing_mode_launches_directly_with_the_same_bits(P):
     assert list(n) == [6, 6, 6]   # every sweep was launched (and timed) separately
     singles(b, 6)
     assert np.array_equal(a.get_psi(), b.get_psi())
+
+
+def test_strang_single_steps(P):
+    """Imaginary time: n single Strang steps (graph) equal one n-step call.  Real time:
+    single steps by the graph equal single steps launched directly (timing on); an
+    n-step call merges the inner half steps and is not the same arithmetic."""
+    a, b = pair(P)
+    for s in (a, b):
+        s.set_splitting("strang")
+    singles(a, 6)
+    b.step_imag(6)
+    assert np.array_equal(a.get_psi(), b.get_psi())
+    P.gp_set_timing(b.handle, True)
+    singles(a, 5, real=True)
+    singles(b, 5, real=True)
+    P.gp_set_timing(b.handle, False)
+    assert np.array_equal(a.get_psi(as_complex=True), b.get_psi(as_complex=True))
