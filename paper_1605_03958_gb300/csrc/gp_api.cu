@@ -306,6 +306,11 @@ struct gp_solver {
   cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
   cudaGraphExec_t strang_exec[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
+  // overlapped field reads (gp_get_psi_f32_async): the device-to-host copy of the
+  // staging area runs on copy_stream; later work that reuses staging waits for copy_done
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ready = nullptr, copy_done = nullptr;
+  bool copy_pending = false;
   bool step_graph = true;            // false once capture failed: direct launches only
   // timing
   bool timing = false;
@@ -965,6 +970,13 @@ template <class R> int steps(gp_solver* s, long nsteps) {
   return s->split == GP_SPLIT_STRANG ? strang_steps<R>(s, nsteps) : lie_steps<R>(s, nsteps);
 }
 
+// Make the solver's stream wait for an overlapped read still copying the staging area.
+void wait_copies(gp_solver* s) {
+  if (!s->copy_pending) return;
+  cudaStreamWaitEvent(s->stream, s->copy_done, 0);
+  s->copy_pending = false;
+}
+
 int check_status(gp_solver* s) {
   int st = 0;
   GP_CUDA(s, cudaMemcpyAsync(&st, s->status, sizeof st, cudaMemcpyDeviceToHost, s->stream));
@@ -1054,6 +1066,12 @@ int gp_create_on(const gp_params* p, void* dev_buf, size_t bytes, void* stream, 
 void gp_destroy(gp_solver* s) {
   if (!s) return;
   if (s->stream || s->base) cudaStreamSynchronize(s->stream);
+  if (s->copy_stream) {
+    cudaStreamSynchronize(s->copy_stream);
+    cudaStreamDestroy(s->copy_stream);
+  }
+  if (s->copy_ready) cudaEventDestroy(s->copy_ready);
+  if (s->copy_done) cudaEventDestroy(s->copy_done);
   for (auto& t : s->pending) {
     cudaEventDestroy(t.start);
     cudaEventDestroy(t.stop);
@@ -1070,6 +1088,7 @@ int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
   if (!(wx > 0) || !(wy > 0) || !(wz > 0) || !std::isfinite(wx) || !std::isfinite(wy) ||
       !std::isfinite(wz))
     return fail(s, GP_ERR_ARG, "Gaussian frequencies must be finite and > 0");
+  wait_copies(s);
   s->is_complex = false;
   FieldParams f = field_params(s);
   f.out = s->scale;
@@ -1085,6 +1104,7 @@ int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
 int gp_set_psi(gp_solver* s, const double* host, int is_complex) {
   if (!s || !host || (is_complex != 0 && is_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
   const size_t N = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
+  wait_copies(s);
   GP_CUDA(s, cudaMemcpyAsync(s->staging, host, N * 8 * (is_complex ? 2 : 1),
                              cudaMemcpyHostToDevice, s->stream));
   s->is_complex = is_complex == 1;
@@ -1099,6 +1119,7 @@ int gp_get_psi(gp_solver* s, double* host, int as_complex) {
   if (!s || !host || (as_complex != 0 && as_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
   if (s->is_complex && !as_complex)
     return fail(s, GP_ERR_STATE, "the field is complex; request it with as_complex = 1");
+  wait_copies(s);
   const size_t N = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
   const FieldParams f = field_params(s);
   cudaError_t e = is_f64(s)
@@ -1120,6 +1141,7 @@ int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex) {
   if (pitch == row) {   // one contiguous host copy
     GP_CUDA(s, cudaMemcpyAsync(s->field, host, rows * row, cudaMemcpyHostToDevice, s->stream));
   } else {              // contiguous host copy to the staging area, pitched copy on the device
+    wait_copies(s);
     GP_CUDA(s, cudaMemcpyAsync(s->staging, host, rows * row, cudaMemcpyHostToDevice, s->stream));
     GP_CUDA(s, cudaMemcpy2DAsync(s->field, pitch, s->staging, row, row, rows, cudaMemcpyDeviceToDevice,
                                  s->stream));
@@ -1134,6 +1156,7 @@ int gp_get_psi_f32(gp_solver* s, float* host, int as_complex) {
   if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_get_psi");
   if (as_complex != (s->is_complex ? 1 : 0))
     return fail(s, GP_ERR_STATE, "as_complex must match the field (0: real, 1: complex)");
+  wait_copies(s);
   const int m = as_complex;
   if (!s->is_complex) {   // fold the pending renormalisation factor into the field
     const FieldParams f = field_params(s);
@@ -1154,14 +1177,41 @@ int gp_get_psi_f32(gp_solver* s, float* host, int as_complex) {
   return check_status(s);
 }
 
+int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex) {
+  if (!s || !host || (as_complex != 0 && as_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_get_psi");
+  if (as_complex != (s->is_complex ? 1 : 0))
+    return fail(s, GP_ERR_STATE, "as_complex must match the field (0: real, 1: complex)");
+  if (!s->copy_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy stream");
+  }
+  wait_copies(s);   // the previous overlapped read may still be copying the staging area
+  const int m = as_complex;
+  const size_t bytes = (size_t)4 * (m + 1) * s->prm.nx * s->prm.ny * s->prm.nz;
+  float* snap = reinterpret_cast<float*>(s->staging);
+  const cudaError_t e = gpk::launch_export_f32(field_params(s), m == 1, snap, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "export");
+  GP_CUDA(s, cudaEventRecord(s->copy_ready, s->stream));
+  GP_CUDA(s, cudaStreamWaitEvent(s->copy_stream, s->copy_ready, 0));
+  GP_CUDA(s, cudaMemcpyAsync(host, snap, bytes, cudaMemcpyDeviceToHost, s->copy_stream));
+  GP_CUDA(s, cudaEventRecord(s->copy_done, s->copy_stream));
+  s->copy_pending = true;
+  return GP_OK;
+}
+
 int gp_step_imag(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
   if (s->is_complex) return fail(s, GP_ERR_STATE, "imaginary-time steps need a real field");
+  wait_copies(s);
   return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
 }
 
 int gp_step_real(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
+  wait_copies(s);
   if (!s->is_complex) {
     const int rc = promote_to_complex(s);
     if (rc != GP_OK) return rc;
@@ -1198,6 +1248,7 @@ int gp_get_g(const gp_solver* s, double* g) {
 
 int gp_observables(gp_solver* s, gp_obs* out) {
   if (!s || !out) return s ? fail(s, GP_ERR_ARG, "out is NULL") : GP_ERR_ARG;
+  wait_copies(s);
   const FieldParams f = field_params(s);
   cudaError_t e = is_f64(s) ? gpk::launch_observables<double>(f, s->is_complex, s->stream)
                             : gpk::launch_observables<float>(f, s->is_complex, s->stream);
@@ -1221,6 +1272,7 @@ int gp_observables(gp_solver* s, gp_obs* out) {
 
 int gp_density2d(gp_solver* s, int plane, double* out) {
   if (!s || !out || plane < 0 || plane > 2) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  wait_copies(s);
   const gp_params& p = s->prm;
   const FieldParams f = field_params(s);
   cudaError_t e = is_f64(s) ? gpk::launch_density2d<double>(f, s->is_complex, plane, s->staging, s->stream)
@@ -1234,6 +1286,7 @@ int gp_density2d(gp_solver* s, int plane, double* out) {
 
 int gp_density1d(gp_solver* s, int axis, double* out) {
   if (!s || !out || axis < 0 || axis > 2) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  wait_copies(s);
   const gp_params& p = s->prm;
   const FieldParams f = field_params(s);
   const int plane = axis == 2 ? 1 : 0;  // x, y from the xy plane; z from the xz plane
@@ -1255,6 +1308,7 @@ int gp_density1d(gp_solver* s, int axis, double* out) {
 
 int gp_sync(gp_solver* s) {
   if (!s) return GP_ERR_ARG;
+  wait_copies(s);
   return check_status(s);
 }
 

@@ -192,6 +192,9 @@ template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaSt
 // psi <- *p.scale psi in place (the caller then sets the factor to 1).
 template <class R> cudaError_t launch_fold_scale(const FieldParams& p, bool complex_field,
                                                  cudaStream_t st);
+// FP32 field times *p.scale, packed into rows of nx elements in dst (not aliasing the
+// field); the field and the factor are left as they are.
+cudaError_t launch_export_f32(const FieldParams& p, bool complex_field, float* dst, cudaStream_t st);
 template <class R> cudaError_t launch_init_gaussian(const FieldParams& p, double wx, double wy,
                                                     double wz, cudaStream_t st);
 template <class R> cudaError_t launch_import(const FieldParams& p, const double* src,

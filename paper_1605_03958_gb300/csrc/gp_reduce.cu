@@ -252,6 +252,32 @@ __global__ void k_fold_scale(const FieldParams p) {
     }
 }
 
+// FP32 field (words = 1 real, 2 complex floats per element) times the pending factor,
+// packed into rows of nx elements in dst (not the field): 16-byte vectors when the
+// rows are contiguous and a multiple of four floats, else one float per thread.
+__global__ void k_export_f32(const FieldParams p, int words, float* __restrict__ dst) {
+  const float s = (float)(*p.scale);
+  const float* src = static_cast<const float*>(p.psi);
+  const size_t rw = (size_t)p.nx * words, pw = (size_t)p.pitch * words;
+  const size_t nrows = (size_t)p.ny * p.nz;
+  if (rw == pw && rw % 4 == 0) {
+    const size_t n4 = nrows * rw / 4;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+      float4 v = s4[i];
+      v.x *= s;
+      v.y *= s;
+      v.z *= s;
+      v.w *= s;
+      d4[i] = v;
+    }
+    return;
+  }
+  for (size_t r = blockIdx.x; r < nrows; r += gridDim.x)
+    for (size_t i = threadIdx.x; i < rw; i += blockDim.x) dst[r * rw + i] = src[r * pw + i] * s;
+}
+
 // ------------------------------------------------------------ initial Gaussian
 
 template <class R>
@@ -414,6 +440,11 @@ template <class R>
 cudaError_t launch_fold_scale(const FieldParams& p, bool complex_field, cudaStream_t st) {
   if (complex_field) k_fold_scale<R, true><<<grid_for_rows(p), 256, 0, st>>>(p);
   else k_fold_scale<R, false><<<grid_for_rows(p), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_f32(const FieldParams& p, bool complex_field, float* dst, cudaStream_t st) {
+  k_export_f32<<<grid_for_rows(p), 256, 0, st>>>(p, complex_field ? 2 : 1, dst);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_get_psi": (i, [vp, vp, i]),
         "gp_set_psi_f32": (i, [vp, vp, i]),
         "gp_get_psi_f32": (i, [vp, vp, i]),
+        "gp_get_psi_f32_async": (i, [vp, vp, i]),
         "gp_step_imag": (i, [vp, l]),
         "gp_step_real": (i, [vp, l]),
         "gp_set_g": (i, [vp, d]),
@@ -220,6 +221,12 @@ def gp_set_psi_f32_ptr(h, host_ptr: int, is_complex: bool) -> None:
 
 def gp_get_psi_f32_ptr(h, host_ptr: int, as_complex: bool) -> None:
     _check(load_library().gp_get_psi_f32(h, ctypes.c_void_p(host_ptr), int(as_complex)), h)
+
+
+def gp_get_psi_f32_async_ptr(h, host_ptr: int, as_complex: bool) -> None:
+    """Overlapped read into caller host memory (page-locked for overlap); the buffer
+    is complete after gp_sync(h)."""
+    _check(load_library().gp_get_psi_f32_async(h, ctypes.c_void_p(host_ptr), int(as_complex)), h)
 
 
 def gp_step_imag(h, nsteps: int) -> None:

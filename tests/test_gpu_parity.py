@@ -393,3 +393,53 @@ def test_fp32_host_io_matches_fp64_host_io(P, orc, mode):
         P.gp.gp_set_psi_f32(f64.handle, psi)
     for s in (a, b, f64):
         s.close()
+
+
+@pytest.mark.parametrize("mode", ["imag", "real"])
+@pytest.mark.parametrize("nx", [40, 37])
+def test_fp32_overlapped_read_equals_synchronous_read(P, orc, mode, nx):
+    """gp_get_psi_f32_async (snapshot into the staging area, copy on the solver's copy
+    stream, complete after gp_sync) against gp_get_psi_f32, contiguous (nx = 40) and
+    padded (nx = 37) rows: the same bits; the solver's state is untouched by the
+    overlapped read, and a put / step / read loop gives the same bits as the
+    synchronous loop (the step waits for the copy before it reuses the staging area)."""
+    import torch
+    p = problem(orc, nx, 29, 23, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=80.0)
+    cplx = mode == "real"
+    a, b = solver(P, p, prec="f32"), solver(P, p, prec="f32")
+    for s in (a, b):
+        s.init_gaussian()
+        s.step_imag(3)
+        if cplx:
+            s.step_real(2)
+    n = p.shape[0] * p.shape[1] * p.shape[2] * (2 if cplx else 1)
+    host = torch.zeros(n, dtype=torch.float32, pin_memory=True)
+    P.gp.gp_get_psi_f32_async_ptr(a.handle, host.data_ptr(), cplx)
+    P.gp.gp_sync(a.handle)
+    want = P.gp.gp_get_psi_f32(b.handle, p.shape, cplx)
+    got = host.numpy().view(np.complex64 if cplx else np.float32).reshape(p.shape)
+    assert np.array_equal(got, want)
+    # a continues without the fold the synchronous read made in b: same bits
+    for s in (a, b):
+        s.step_imag(4) if mode == "imag" else s.step_real(4)
+    assert np.array_equal(P.gp.gp_get_psi_f32(a.handle, p.shape, cplx),
+                          P.gp.gp_get_psi_f32(b.handle, p.shape, cplx))
+    # put / step / read loops
+    src = torch.from_numpy(np.ascontiguousarray(want).view(np.float32).reshape(-1).copy()).pin_memory()
+    outs = []
+    for k in range(4):
+        P.gp.gp_set_psi_f32_ptr(a.handle, src.data_ptr(), cplx)
+        a.step_imag(1) if mode == "imag" else a.step_real(1)
+        o = torch.zeros(n, dtype=torch.float32, pin_memory=True)
+        P.gp.gp_get_psi_f32_async_ptr(a.handle, o.data_ptr(), cplx)
+        outs.append(o)
+    P.gp.gp_sync(a.handle)
+    P.gp.gp_set_psi_f32_ptr(b.handle, src.data_ptr(), cplx)
+    b.step_imag(1) if mode == "imag" else b.step_real(1)
+    ref = P.gp.gp_get_psi_f32(b.handle, p.shape, cplx)
+    for o in outs:
+        assert np.array_equal(o.numpy().view(np.complex64 if cplx else np.float32).reshape(p.shape), ref)
+    with pytest.raises(P.GPError):
+        P.gp.gp_get_psi_f32_async_ptr(a.handle, host.data_ptr(), not cplx)
+    for s in (a, b):
+        s.close()
