@@ -164,7 +164,10 @@ int gp_get_psi_f32(gp_solver* s, float* host, int as_complex);
 int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex);
 
 /* nsteps imaginary-time SSCN steps on the real field, each renormalised to unit
- * norm.  GP_ERR_STATE on a complex field.  Asynchronous.                         */
+ * norm.  GP_ERR_STATE on a complex field.  Asynchronous.  A call of one step
+ * replays a CUDA graph of the step's launches, captured on the first such call (per
+ * mode and splitting) on a stream of the solver's own; while the caller captures the
+ * solver's stream, or if the capture fails, the step is launched directly.        */
 int gp_step_imag(gp_solver* s, long nsteps);
 
 /* nsteps real-time SSCN steps on the complex field.  On a real field the field is

@@ -857,6 +857,17 @@ void drop_step_graphs(gp_solver* s) {
 
 // Capture the launches fn makes on s->stream into *exec, on the side stream; on any
 // failure the solver falls back to direct launches for good.
+// True when the solver's stream is being captured by the caller: a step then records
+// its launches into the caller's graph directly.
+bool caller_capturing(const gp_solver* s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s->stream, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
 template <class Fn> void capture_graph(gp_solver* s, cudaGraphExec_t* exec, Fn fn) {
   if (!s->cap_stream &&
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -890,7 +901,7 @@ template <class Fn> void capture_graph(gp_solver* s, cudaGraphExec_t* exec, Fn f
 // (graphs replayed back to back would serialise there).  The graph holds the sweep
 // parameters by value: gp_set_g drops it.
 template <class R> int lie_steps(gp_solver* s, long nsteps) {
-  if (nsteps == 1 && s->step_graph && !s->timing && !s->kinetic_only) {
+  if (nsteps == 1 && s->step_graph && !s->timing && !s->kinetic_only && !caller_capturing(s)) {
     const int m = s->is_complex ? 1 : 0;
     if (!s->step_exec[m]) capture_graph(s, &s->step_exec[m], [s] { return lie_step_direct<R>(s); });
     if (s->step_exec[m]) {
@@ -954,7 +965,7 @@ template <class R> int strang_steps_direct(gp_solver* s, long nsteps) {
 
 // A single Strang step replays its graph, like a single Lie step.
 template <class R> int strang_steps(gp_solver* s, long nsteps) {
-  if (nsteps == 1 && s->step_graph && !s->timing) {
+  if (nsteps == 1 && s->step_graph && !s->timing && !caller_capturing(s)) {
     const int m = s->is_complex ? 1 : 0;
     if (!s->strang_exec[m])
       capture_graph(s, &s->strang_exec[m], [s] { return strang_steps_direct<R>(s, 1); });
