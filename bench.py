@@ -284,8 +284,8 @@ def run_cuda(args):
     # host memory, one step, D2H of the resulting field into pinned host memory; the
     # host buffers are in the field's own precision (FP32 I/O for an FP32 solve).
     # FP32: the read is the overlapped one (its device-to-host copy runs beside the next
-    # step's host-to-device copy) and gp_sync completes the last read before the clock
-    # stops.
+    # step's host-to-device copy and the next step) and gp_sync completes the last read
+    # before the clock stops.
     e2e = None
     if args.e2e_steps > 0:
         f32 = sbytes == 4

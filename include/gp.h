@@ -149,17 +149,18 @@ int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex);
 int gp_get_psi_f32(gp_solver* s, float* host, int as_complex);
 
 /* Overlapped read of an FP32 solver's field into host (same layout as
- * gp_get_psi_f32).  The field times the pending renormalisation factor is packed
- * into the solver's staging area on the device (the solver's state is left as it
- * is), and the device-to-host copy of that snapshot runs on the solver's own copy
- * stream: it overlaps whatever the caller enqueues next that does not reuse the
- * staging area, typically the next gp_set_psi_f32 of a contiguous field, whose
- * host-to-device copy runs in the other direction at the same time.  Every later
- * call that reuses the staging area (steps, reads, observables, densities, the
- * Gaussian init, gp_set_psi, gp_sync) first makes the solver's stream wait for the
- * copy.  host is complete only after gp_sync(s) (or gp_destroy); it should be
- * page-locked for the copy to be asynchronous.  Does not read the status flag
- * (gp_sync does).  Same argument errors as gp_get_psi_f32; GP_ERR_CUDA if the copy
+ * gp_get_psi_f32).  The field times the pending renormalisation factor is packed on
+ * the device into a snapshot buffer of the solver (8 bytes per grid point,
+ * cudaMalloc'd on the first call and freed by gp_destroy; the solver's state is left
+ * as it is), and the device-to-host copy of the snapshot runs on the solver's own
+ * copy stream: it overlaps whatever the caller enqueues next — the next
+ * gp_set_psi_f32, whose host-to-device copy runs in the other direction at the same
+ * time, and the next steps.  The next overlapped read waits for the previous copy
+ * before it packs; gp_sync(s) waits for it too, and so do the synchronous reads,
+ * observables and densities.  host is complete only after gp_sync(s) (or
+ * gp_destroy); it should be page-locked for the copy to be asynchronous.  Does not
+ * read the status flag (gp_sync does).  Same argument errors as gp_get_psi_f32;
+ * GP_ERR_NOMEM if the snapshot buffer cannot be allocated, GP_ERR_CUDA if the copy
  * stream cannot be created.                                                        */
 int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex);
 

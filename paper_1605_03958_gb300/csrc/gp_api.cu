@@ -306,8 +306,10 @@ struct gp_solver {
   cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
   cudaGraphExec_t strang_exec[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
-  // overlapped field reads (gp_get_psi_f32_async): the device-to-host copy of the
-  // staging area runs on copy_stream; later work that reuses staging waits for copy_done
+  // overlapped field reads (gp_get_psi_f32_async): the field is packed into export_buf
+  // (allocated on first use) and copied to host on copy_stream; the next packing and the
+  // host-completing calls wait for copy_done
+  void* export_buf = nullptr;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_ready = nullptr, copy_done = nullptr;
   bool copy_pending = false;
@@ -981,7 +983,7 @@ template <class R> int steps(gp_solver* s, long nsteps) {
   return s->split == GP_SPLIT_STRANG ? strang_steps<R>(s, nsteps) : lie_steps<R>(s, nsteps);
 }
 
-// Make the solver's stream wait for an overlapped read still copying the staging area.
+// Make the solver's stream wait for an overlapped read still copying its snapshot.
 void wait_copies(gp_solver* s) {
   if (!s->copy_pending) return;
   cudaStreamWaitEvent(s->stream, s->copy_done, 0);
@@ -1083,6 +1085,7 @@ void gp_destroy(gp_solver* s) {
   }
   if (s->copy_ready) cudaEventDestroy(s->copy_ready);
   if (s->copy_done) cudaEventDestroy(s->copy_done);
+  if (s->export_buf) cudaFree(s->export_buf);
   for (auto& t : s->pending) {
     cudaEventDestroy(t.start);
     cudaEventDestroy(t.stop);
@@ -1099,7 +1102,6 @@ int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
   if (!(wx > 0) || !(wy > 0) || !(wz > 0) || !std::isfinite(wx) || !std::isfinite(wy) ||
       !std::isfinite(wz))
     return fail(s, GP_ERR_ARG, "Gaussian frequencies must be finite and > 0");
-  wait_copies(s);
   s->is_complex = false;
   FieldParams f = field_params(s);
   f.out = s->scale;
@@ -1115,7 +1117,6 @@ int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
 int gp_set_psi(gp_solver* s, const double* host, int is_complex) {
   if (!s || !host || (is_complex != 0 && is_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
   const size_t N = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
-  wait_copies(s);
   GP_CUDA(s, cudaMemcpyAsync(s->staging, host, N * 8 * (is_complex ? 2 : 1),
                              cudaMemcpyHostToDevice, s->stream));
   s->is_complex = is_complex == 1;
@@ -1152,7 +1153,6 @@ int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex) {
   if (pitch == row) {   // one contiguous host copy
     GP_CUDA(s, cudaMemcpyAsync(s->field, host, rows * row, cudaMemcpyHostToDevice, s->stream));
   } else {              // contiguous host copy to the staging area, pitched copy on the device
-    wait_copies(s);
     GP_CUDA(s, cudaMemcpyAsync(s->staging, host, rows * row, cudaMemcpyHostToDevice, s->stream));
     GP_CUDA(s, cudaMemcpy2DAsync(s->field, pitch, s->staging, row, row, rows, cudaMemcpyDeviceToDevice,
                                  s->stream));
@@ -1199,10 +1199,16 @@ int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(s, e, "copy stream");
   }
-  wait_copies(s);   // the previous overlapped read may still be copying the staging area
+  const size_t npts = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
+  if (!s->export_buf && cudaMalloc(&s->export_buf, 8 * npts) != cudaSuccess) {   // a packed complex field
+    cudaGetLastError();
+    s->export_buf = nullptr;
+    return fail(s, GP_ERR_NOMEM, "no device memory for the snapshot of an overlapped read");
+  }
+  wait_copies(s);   // the previous overlapped read may still be copying the snapshot
   const int m = as_complex;
-  const size_t bytes = (size_t)4 * (m + 1) * s->prm.nx * s->prm.ny * s->prm.nz;
-  float* snap = reinterpret_cast<float*>(s->staging);
+  const size_t bytes = (size_t)4 * (m + 1) * npts;
+  float* snap = static_cast<float*>(s->export_buf);
   const cudaError_t e = gpk::launch_export_f32(field_params(s), m == 1, snap, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "export");
   GP_CUDA(s, cudaEventRecord(s->copy_ready, s->stream));
@@ -1216,13 +1222,11 @@ int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex) {
 int gp_step_imag(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
   if (s->is_complex) return fail(s, GP_ERR_STATE, "imaginary-time steps need a real field");
-  wait_copies(s);
   return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
 }
 
 int gp_step_real(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
-  wait_copies(s);
   if (!s->is_complex) {
     const int rc = promote_to_complex(s);
     if (rc != GP_OK) return rc;

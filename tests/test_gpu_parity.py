@@ -398,11 +398,11 @@ def test_fp32_host_io_matches_fp64_host_io(P, orc, mode):
 @pytest.mark.parametrize("mode", ["imag", "real"])
 @pytest.mark.parametrize("nx", [40, 37])
 def test_fp32_overlapped_read_equals_synchronous_read(P, orc, mode, nx):
-    """gp_get_psi_f32_async (snapshot into the staging area, copy on the solver's copy
-    stream, complete after gp_sync) against gp_get_psi_f32, contiguous (nx = 40) and
-    padded (nx = 37) rows: the same bits; the solver's state is untouched by the
-    overlapped read, and a put / step / read loop gives the same bits as the
-    synchronous loop (the step waits for the copy before it reuses the staging area)."""
+    """gp_get_psi_f32_async (snapshot on the device, copy on the solver's copy stream,
+    complete after gp_sync) against gp_get_psi_f32, contiguous (nx = 40) and padded
+    (nx = 37) rows: the same bits; the solver's state is untouched by the overlapped
+    read, and a put / step / read loop — each read's copy running beside the next put
+    and step — gives the same bits as the synchronous loop."""
     import torch
     p = problem(orc, nx, 29, 23, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=80.0)
     cplx = mode == "real"
