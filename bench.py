@@ -7,9 +7,10 @@ Gaussian.  One benchmark step is one full SSCN time step: pointwise substep, CN
 sweeps along x, y and z, norm and renormalisation factor.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the
-solver's stream; a 256 MiB device buffer is rewritten between timed steps so that
-every step starts with a cold L2 (the FP32 field is 31 MB, below the 135 MB L2).
-Per-sweep durations come from the library's own events on the same stream.
+solver's stream; between timed steps (outside the events) a 256 MiB device buffer is
+written and another 256 MiB read, so that every step starts with a cold L2 (the FP32
+field is 31 MB, below the 129 MB L2).  Per-sweep durations come from a second pass
+with the library's own events on the same stream.
 `value` = (ranks x grid points x K) / max over ranks of the summed step time.
 
 Multi-GPU: every rank runs an independent replica of the solve (the solve itself
