@@ -40,6 +40,7 @@ WORKLOAD = "imag3d 240x200x160, h=0.1, dt=0.1h^2, trap (1,1.41,2), g=100, imagin
 
 
 def parse():
+    global NX, NY, NZ, NPTS, WORKLOAD, DT
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -60,11 +61,18 @@ def parse():
                     help="batch: steps per instance timed for the one-at-a-time baselines")
     ap.add_argument("--splitting", choices=["lie", "strang"], default="lie",
                     help="splitting of a step (single workload)")
+    ap.add_argument("--mode", choices=["imag", "real"], default="imag",
+                    help="single workload: imag (ground state, default) or real: the quench "
+                         "dynamics workload (dt = 0.02 h^2; 300 imaginary steps at g = 100 from "
+                         "the Gaussian, then g = 200 and timed real-time steps on the complex field)")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="override the grid (profiling of out-of-L2 cases); h and dt unchanged")
     args = ap.parse_args()
+    if args.mode == "real":
+        DT = 0.02 * H * H
+        WORKLOAD = ("real3d 240x200x160, h=0.1, dt=0.02h^2, trap (1,1.41,2), ground state at "
+                    "g=100 then quench to g=200, real time")
     if args.grid:
-        global NX, NY, NZ, NPTS, WORKLOAD
         NX, NY, NZ = args.grid
         NPTS = NX * NY * NZ
         WORKLOAD = WORKLOAD.replace("240x200x160", f"{NX}x{NY}x{NZ}")
@@ -200,11 +208,19 @@ def run_cuda(args):
     def max_over_ranks(x):
         return replica_throughput(x, 1, device="cuda")[1]
 
-    sbytes = 4 if args.prec == "f32" else 8
-    s = P.Solver(NX, NY, NZ, H, dt=DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G,
-                 prec=args.prec)
-    s.set_splitting(args.splitting)
-    s.init_gaussian()
+    real = args.mode == "real"
+    sbytes = (4 if args.prec == "f32" else 8) * (2 if real else 1)   # bytes per stored point
+
+    def make_solver(prec):
+        so = P.Solver(NX, NY, NZ, H, dt=DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G, prec=prec)
+        so.set_splitting(args.splitting)
+        so.init_gaussian()
+        if real:   # the quench: ground state at g, then 2 g in real time
+            so.step_imag(300)
+            so.set_g(2 * G)
+        return so, (so.step_real if real else so.step_imag)
+
+    s, step = make_solver(args.prec)
     flush_w = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     flush_r = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -216,7 +232,7 @@ def run_cuda(args):
         flush_r.sum()
 
     for _ in range(max(args.warmup, 3)):
-        s.step_imag(1)
+        step(1)
         flush()
     s.sync()
     torch.cuda.synchronize()
@@ -230,7 +246,7 @@ def run_cuda(args):
         barrier()
         for k in range(K):
             ev0[k].record()
-            s.step_imag(1)
+            step(1)
             ev1[k].record()
             flush()
         torch.cuda.synchronize()
@@ -246,7 +262,7 @@ def run_cuda(args):
     P.gp_set_timing(s.handle, True)
     torch.cuda.synchronize()
     for k in range(K2):
-        s.step_imag(1)
+        step(1)
         flush()
     kms, kn = P.gp_get_timing(s.handle)
     P.gp_set_timing(s.handle, False)
@@ -256,15 +272,17 @@ def run_cuda(args):
     hbm, peak_kind = peaks()
     names = ["sweep_x", "sweep_y", "sweep_z"]
     info = s.info()
-    rt = "float" if sbytes == 4 else "double"
+    rt = "float" if args.prec == "f32" else "double"
     L = info["trunc"]
+    c = "true" if real else "false"     # complex field
+    nm = "false" if real else "true"    # the z sweep sums the norm in imaginary time only
     kernels = {
-        "sweep_x": (f"k_sweep_x_band<float,false,{info['band_w']}>" if info["band_mask"] & 1 else
-                    f"k_sweep_x_stream<float,false,{L}>" if info["fast_mask"] & 1 else f"k_sweep_x<{rt},false>"),
-        "sweep_y": (f"k_sweep_band_line<float,false,1,false,{info['band_w']}>" if info["band_mask"] & 2 else
-                    f"k_sweep_stream<float,false,1,false,{L}>" if info["fast_mask"] & 2 else f"k_sweep_y<{rt},false>"),
-        "sweep_z": (f"k_sweep_band_line<float,false,2,true,{info['band_w']}>" if info["band_mask"] & 4 else
-                    f"k_sweep_stream<float,false,2,true,{L}>" if info["fast_mask"] & 4 else f"k_sweep_z<{rt},false,true>")}
+        "sweep_x": (f"k_sweep_x_band<float,{c},{info['band_w']}>" if info["band_mask"] & 1 else
+                    f"k_sweep_x_stream<float,{c},{L}>" if info["fast_mask"] & 1 else f"k_sweep_x<{rt},{c}>"),
+        "sweep_y": (f"k_sweep_band_line<float,{c},1,false,{info['band_w']}>" if info["band_mask"] & 2 else
+                    f"k_sweep_stream<float,{c},1,false,{L}>" if info["fast_mask"] & 2 else f"k_sweep_y<{rt},{c}>"),
+        "sweep_z": (f"k_sweep_band_line<float,{c},2,{nm},{info['band_w']}>" if info["band_mask"] & 4 else
+                    f"k_sweep_stream<float,{c},2,{nm},{L}>" if info["fast_mask"] & 4 else f"k_sweep_z<{rt},{c},{nm}>")}
     per = {}
     for i, n in enumerate(names):
         if kn[i] == 0:   # a 2D solve has no z sweep
@@ -289,26 +307,27 @@ def run_cuda(args):
     # before the clock stops.
     e2e = None
     if args.e2e_steps > 0:
-        f32 = sbytes == 4
+        f32 = args.prec == "f32"
         hdt = torch.float32 if f32 else torch.float64
         put = P.gp.gp_set_psi_f32_ptr if f32 else P.gp.gp_set_psi_ptr
         get = P.gp.gp_get_psi_f32_async_ptr if f32 else P.gp.gp_get_psi_ptr
-        host_in = torch.empty(NPTS, dtype=hdt, pin_memory=True)
-        host_out = torch.empty(NPTS, dtype=hdt, pin_memory=True)
-        get(s.handle, host_in.data_ptr(), False)
+        nh = NPTS * (2 if real else 1)
+        host_in = torch.empty(nh, dtype=hdt, pin_memory=True)
+        host_out = torch.empty(nh, dtype=hdt, pin_memory=True)
+        get(s.handle, host_in.data_ptr(), real)
         P.gp.gp_sync(s.handle)
         for _ in range(3):
-            put(s.handle, host_in.data_ptr(), False)
-            s.step_imag(1)
-            get(s.handle, host_out.data_ptr(), False)
+            put(s.handle, host_in.data_ptr(), real)
+            step(1)
+            get(s.handle, host_out.data_ptr(), real)
         P.gp.gp_sync(s.handle)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            put(s.handle, host_in.data_ptr(), False)
-            s.step_imag(1)
-            get(s.handle, host_out.data_ptr(), False)
+            put(s.handle, host_in.data_ptr(), real)
+            step(1)
+            get(s.handle, host_out.data_ptr(), real)
         P.gp.gp_sync(s.handle)
         torch.cuda.synchronize()
         barrier()
@@ -317,7 +336,7 @@ def run_cuda(args):
         e2e = {"value": round(world * NPTS * args.e2e_steps / e2e_s, 1), "unit": "grid-point-steps/s",
                "h2d_bytes_per_step": NPTS * sbytes, "d2h_bytes_per_step": NPTS * sbytes,
                "steps": args.e2e_steps,
-               "api": (f"gp_set_psi{name}(pinned host field) + gp_step_imag(1) + "
+               "api": (f"gp_set_psi{name}(pinned host field) + gp_step_{args.mode}(1) + "
                        f"gp_get_psi{name}{'_async' if f32 else ''}(pinned)"
                        + ("; gp_sync after the last step" if f32 else ""))}
 
@@ -325,7 +344,7 @@ def run_cuda(args):
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    s.step_imag(K)
+    step(K)
     b.record()
     torch.cuda.synchronize()
     warm_ms = a.elapsed_time(b) / K
@@ -334,10 +353,9 @@ def run_cuda(args):
     other = None
     if args.f64_steps > 0:
         oprec = "f64" if args.prec == "f32" else "f32"
-        so = P.Solver(NX, NY, NZ, H, dt=DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G, prec=oprec)
-        so.init_gaussian()
+        so, ostep = make_solver(oprec)
         for _ in range(3):
-            so.step_imag(1)
+            ostep(1)
             flush()
         torch.cuda.synchronize()
         P.gp_set_timing(so.handle, True)
@@ -345,14 +363,14 @@ def run_cuda(args):
         e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.f64_steps)]
         for k in range(args.f64_steps):
             e0[k].record()
-            so.step_imag(1)
+            ostep(1)
             e1[k].record()
             flush()
         torch.cuda.synchronize()
         oms, okn = P.gp_get_timing(so.handle)
         so.sync()
         ototal = sum(e0[k].elapsed_time(e1[k]) for k in range(args.f64_steps))
-        ob = 8 if oprec == "f64" else 4
+        ob = (8 if oprec == "f64" else 4) * (2 if real else 1)
         other = {"prec": oprec, "value": round(NPTS * args.f64_steps / (ototal / 1e3), 1),
                  "ms_per_step": round(ototal / args.f64_steps, 5), "steps": args.f64_steps,
                  "sweeps_avg_ms": [round(oms[i] / max(okn[i], 1), 5) for i in range(3)],
@@ -363,15 +381,16 @@ def run_cuda(args):
     obs = s.observables()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(real)
 
     line = {
         "metric": "grid-point SSCN steps/s", "value": round(value, 1),
         "unit": "grid-point-steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(total_ms / K, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "vs_baseline": None, "dtype": {"f32": "c64", "f64": "c128"}[args.prec] if real else args.prec,
+        "data": "synthetic",
         "config": {"workload": WORKLOAD + ("" if args.splitting == "lie" else ", Strang splitting"),
-                   "grid": [NX, NY, NZ], "field": args.prec,
+                   "grid": [NX, NY, NZ], "field": {"f32": "c64", "f64": "c128"}[args.prec] if real else args.prec,
                    "reductions": "f64", "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write + 256 MiB read, untimed)",
                    "steps_per_sample": 1},
@@ -394,29 +413,33 @@ def run_cuda(args):
 
 # ------------------------------------------------------- CPU oracle timings
 
-def _oracle_sample(nz_s, steps, threads):
+def _oracle_sample(nz_s, steps, threads, real=False):
     import oracle
     oracle.set_threads(threads)
-    p = oracle.Problem(NX, NY, nz_s, H, H, H, DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G)
+    p = oracle.Problem(NX, NY, nz_s, H, H, H, DT, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2],
+                       g=2 * G if real else G)
     psi = oracle.init_gaussian(p)
+    if real:
+        psi = psi.astype(complex)
     t0 = time.perf_counter()
-    oracle.step_imag(p, psi, steps)
+    (oracle.step_real if real else oracle.step_imag)(p, psi, steps)
     return time.perf_counter() - t0
 
 
-def cpu_baseline():
+def cpu_baseline(real=False):
     """The oracle as it stands on this host's cores, full grid, bounded to ~20 s."""
     threads = os.cpu_count() or 1
-    t1 = _oracle_sample(NZ, 1, threads)
+    t1 = _oracle_sample(NZ, 1, threads, real)
     steps = max(1, min(100, int(20.0 / max(t1, 1e-3))))
-    t = _oracle_sample(NZ, steps, threads)
-    ts = _oracle_sample(NZ, 1, 1)
+    t = _oracle_sample(NZ, steps, threads, real)
+    ts = _oracle_sample(NZ, 1, 1, real)
+    kind = "real-time" if real else "imaginary-time"
     return {"value": round(NPTS * steps / t, 1), "unit": "grid-point-steps/s", "cores": threads,
             "kind": "oracle",
-            "sample": f"{steps} FP64 imaginary-time steps of the full 240x200x160 grid, "
+            "sample": f"{steps} FP64 {kind} steps of the full 240x200x160 grid, "
                       f"OpenMP over line solves on {threads} threads",
             "single_thread": {"value": round(NPTS / ts, 1), "unit": "grid-point-steps/s",
-                              "cores": 1, "sample": "1 FP64 imaginary-time step of the full grid"}}
+                              "cores": 1, "sample": f"1 FP64 {kind} step of the full grid"}}
 
 
 def run_reference(args):
@@ -428,18 +451,19 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     # each step: one oracle SSCN step on a 240x200xnz_s slab of the grid, nz_s sized so
     # that the whole warm-up + timed run stays near 90 s of CPU time
-    probe = _oracle_sample(16, 1, threads) / 16.0          # seconds per z-plane-step
+    real = args.mode == "real"
+    probe = _oracle_sample(16, 1, threads, real) / 16.0    # seconds per z-plane-step
     budget = 90.0 / max(args.steps + args.warmup, 1)
     nz_s = int(max(3, min(NZ, budget / max(probe, 1e-9))))
     if args.warmup:
-        _oracle_sample(nz_s, args.warmup, threads)
-    t = _oracle_sample(nz_s, args.steps, threads)
+        _oracle_sample(nz_s, args.warmup, threads, real)
+    t = _oracle_sample(nz_s, args.steps, threads, real)
     value = NX * NY * nz_s * args.steps / t
     line = {"impl": "reference", "metric": "grid-point SSCN steps/s", "value": round(value, 1),
             "unit": "grid-point-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128" if real else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "sample_grid": [NX, NY, nz_s]},
             "cpu_baseline": {"value": round(value, 1), "unit": "grid-point-steps/s",
                              "cores": threads, "kind": "oracle",
