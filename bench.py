@@ -149,11 +149,18 @@ class ClockSampler:
 
 
 def source_hash():
+    """Hash of the code (comments and blank space removed) of the files that define the
+    sweep kernels and their launch shapes: ncu figures stay tied to the code they were
+    taken on, and an edit of a comment does not void them."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("gp_sweeps.cu", "gp_device.cuh", "gp_internal.h", "gp_api.cu"):
-        with open(os.path.join(ROOT, "paper_1605_03958_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1605_03958_gb300", "csrc", f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -857,8 +857,6 @@ void drop_step_graphs(gp_solver* s) {
     }
 }
 
-// Capture the launches fn makes on s->stream into *exec, on the side stream; on any
-// failure the solver falls back to direct launches for good.
 // True when the solver's stream is being captured by the caller: a step then records
 // its launches into the caller's graph directly.
 bool caller_capturing(const gp_solver* s) {
@@ -870,6 +868,8 @@ bool caller_capturing(const gp_solver* s) {
   return st != cudaStreamCaptureStatusNone;
 }
 
+// Capture the launches fn makes on s->stream into *exec, on the side stream; on any
+// failure the solver falls back to direct launches for good.
 template <class Fn> void capture_graph(gp_solver* s, cudaGraphExec_t* exec, Fn fn) {
   if (!s->cap_stream &&
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
