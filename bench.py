@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--f64-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "serve", "c1"], default="single",
                     help="single: the 240x200x160 solve (default); batch: 64 uneven FP32 "
                          "solves resident in one pool; serve: the continuous-batching server "
-                         "on a Poisson request stream")
+                         "on a Poisson request stream; c1: the plain FP64 64x48x32 ground "
+                         "state (2000 steps, L2-resident, steps/s and observables vs the oracle)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-compare", type=int, default=100,
                     help="serve: leading requests also served one at a time in FP64 and FP32")
@@ -481,6 +482,81 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------ plain FP64 ground state
+
+def run_c1(args):
+    """The small plain-FP64 ground state: 64 x 48 x 32, h = 0.2, dt = 0.1 h^2, trap
+    (1, 1.5, 2), g = 20, 2000 imaginary steps from the Gaussian.  The field (0.8 MB)
+    lives in L2 and a step is a few launches, so the figure is steps/s of back-to-back
+    steps (one call of 2000 steps, and 2000 single-step calls replaying the step's
+    graph), not a fraction of HBM bandwidth.  The observables after 2000 steps are set
+    beside the oracle's, computed on the host cores in the same run."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_03958_gb300 as P
+    import oracle
+    nx, ny, nz, h, dt, trap, g, K = 64, 48, 32, 0.2, 0.004, (1.0, 1.5, 2.0), 20.0, 2000
+    prec = "f64"   # the plain FP64 workload
+    npts = nx * ny * nz
+
+    def solver():
+        so = P.Solver(nx, ny, nz, h, dt=dt, gamma=trap[0], nu=trap[1], lam=trap[2], g=g, prec=prec)
+        so.init_gaussian()
+        return so
+
+    s = solver()
+    s.step_imag(20)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        s2 = solver()
+        torch.cuda.synchronize()
+        a.record()
+        s2.step_imag(K)
+        b.record()
+        torch.cuda.synchronize()
+        one_call_ms = a.elapsed_time(b)
+        s3 = solver()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(K):
+            s3.step_imag(1)
+        b.record()
+        torch.cuda.synchronize()
+        single_ms = a.elapsed_time(b)
+    obs = s2.observables()
+    same = bool(np.array_equal(s2.get_psi(), s3.get_psi()))
+    oracle.set_threads(os.cpu_count() or 1)
+    p = oracle.Problem(nx, ny, nz, h, h, h, dt, gamma=trap[0], nu=trap[1], lam=trap[2], g=g)
+    t0 = time.perf_counter()
+    ref = oracle.step_imag(p, oracle.init_gaussian(p), K)
+    cpu_s = time.perf_counter() - t0
+    ro = oracle.observables(p, ref)
+    keys = ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z", "rms_r")
+    line = {"metric": "grid-point SSCN steps/s", "value": round(npts * K / (one_call_ms / 1e3), 1),
+            "unit": "grid-point-steps/s", "n_gpus": 1, "steps": K, "warmup": 20,
+            "ms_per_step": round(one_call_ms / K, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": "imag3d 64x48x32, h=0.2, dt=0.1h^2, trap (1,1.5,2), g=20, "
+                                   "2000 imaginary steps from the Gaussian",
+                       "l2": "resident (0.8 MB field): steps back to back, no flush"},
+            "steps_per_s": {"one_call": round(K / (one_call_ms / 1e3), 1),
+                            "single_step_calls_graph": round(K / (single_ms / 1e3), 1)},
+            "single_calls_same_bits": same,
+            "observables": {k: obs[k] for k in keys},
+            "oracle_observables": {k: ro[k] for k in keys},
+            "mu_rel_vs_oracle": abs(obs["mu"] - ro["mu"]) / abs(ro["mu"]),
+            "cpu_baseline": {"value": round(npts * K / cpu_s, 1), "unit": "grid-point-steps/s",
+                             "cores": os.cpu_count() or 1, "kind": "oracle",
+                             "sample": "the same 2000 FP64 steps, OpenMP over line solves"},
+            "clocks": clk.summary()}
+    for so in (s, s2, s3):
+        so.close()
+    print(json.dumps(line))
+
+
 # ------------------------------------------------------------ batched solves
 
 def run_batch(args):
@@ -634,6 +710,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c1":
+        run_c1(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":
