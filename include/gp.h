@@ -173,7 +173,8 @@ int gp_step_imag(gp_solver* s, long nsteps);
 
 /* nsteps real-time SSCN steps on the complex field.  On a real field the field is
  * first promoted to complex (imaginary parts zero): the imaginary-to-real-time
- * hand-off of the paper's real-time programs.  Asynchronous.                     */
+ * hand-off of the paper's real-time programs.  Asynchronous.  A call of one step
+ * replays the step's CUDA graph as gp_step_imag does.                            */
 int gp_step_real(gp_solver* s, long nsteps);
 
 /* Replace the nonlinearity g (the paper's quench: the real-time run multiplies g

@@ -1193,11 +1193,21 @@ int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex) {
   if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_get_psi");
   if (as_complex != (s->is_complex ? 1 : 0))
     return fail(s, GP_ERR_STATE, "as_complex must match the field (0: real, 1: complex)");
-  if (!s->copy_stream) {
-    cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(s, e, "copy stream");
+  if (!s->copy_stream) {   // the copy stream and its two events, all or none
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (done) cudaEventDestroy(done);
+      if (ready) cudaEventDestroy(ready);
+      if (cs) cudaStreamDestroy(cs);
+      return cuda_fail(s, e, "copy stream");
+    }
+    s->copy_stream = cs;
+    s->copy_ready = ready;
+    s->copy_done = done;
   }
   const size_t npts = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
   if (!s->export_buf && cudaMalloc(&s->export_buf, 8 * npts) != cudaSuccess) {   // a packed complex field
