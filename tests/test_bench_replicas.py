@@ -46,3 +46,42 @@ def test_single_process_is_identity():
     import bench
     value, ms = bench.replica_throughput(250.0, 1000)
     assert ms == 250.0 and value == pytest.approx(4000.0)
+
+
+def test_source_hash_ignores_comments_and_follows_code(tmp_path, monkeypatch):
+    """The ncu figures in profiles/ncu_traffic.json are keyed to the code of the kernel
+    sources: a comment edit keeps the key, a code edit changes it."""
+    import shutil
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(tmp_path, "paper_1605_03958_gb300", "csrc")
+    os.makedirs(csrc)
+    for f in ("gp_sweeps.cu", "gp_device.cuh", "gp_internal.h", "gp_api.cu"):
+        shutil.copy(os.path.join(root, "paper_1605_03958_gb300", "csrc", f), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.source_hash()
+    api = os.path.join(csrc, "gp_api.cu")
+    src = open(api).read()
+    open(api, "w").write(src + "\n// a comment\n/* another\n   one */\n")
+    assert bench.source_hash() == h0
+    open(api, "w").write(src + "\nstatic int an_extra_definition = 1;\n")
+    assert bench.source_hash() != h0
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """`bench.py --impl reference` prints one JSON line with the contract's keys, the
+    oracle timed on this host's cores (a z-slab sample of the grid)."""
+    import json
+    import sys
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1",
+                                      "--warmup", "0"])
+    monkeypatch.setattr(bench, "_oracle_sample",
+                        lambda nz_s, steps, threads, real=False: 1e-3 * nz_s * max(steps, 1))
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
