@@ -243,6 +243,9 @@ int gp_get_info(const gp_solver* s, long long info[8]);
  *              elements (>= nx); prec GP_F64 (double) or GP_F32 (float); is_complex 1
  *              for interleaved (re, im) values.  The field is used as it is (no
  *              pending renormalisation).
+ *   nx, ny, nz extents as in gp_params: 3..2048 each, or nz = 1 for a 2D field in
+ *              the xy plane (then dz and lambda are ignored, z = 0, the cell area is
+ *              dx dy and there is no z kinetic term, as for a 2D solver).
  *   dx..lambda, g   grid spacings, trap ratios and nonlinearity, as in gp_params.
  *   out        device pointer to 10 doubles, written in gp_obs order with the gp_obs
  *              definitions, once `stream` (a cudaStream_t, or NULL) reaches the work;
@@ -252,7 +255,7 @@ int gp_get_info(const gp_solver* s, long long info[8]);
  * whose work may overlap on the GPU (different streams with no ordering) race on it;
  * issue them on one stream.  The first call on a device looks up that array's device
  * address, which can load the library's GPU code: make this first call before any
- * stream capture begins.  Extents beyond 1..2048 or pitch < nx return GP_ERR_ARG,
+ * stream capture begins.  Other extents or pitch < nx return GP_ERR_ARG,
  * with the reason in gp_last_error(NULL).  No cudaMalloc / cudaFree is called.
  * The paper has no counterpart; this is an operational variant of gp_observables.  */
 int gp_observables_noalloc(const void* psi, int nx, int ny, int nz, long long pitch,

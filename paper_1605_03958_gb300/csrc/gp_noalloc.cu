@@ -172,12 +172,16 @@ __global__ void __launch_bounds__(kThreads) k_observables_noalloc(const Args a) 
   __syncthreads();
   if (threadIdx.x == 0) {
     *a.counter = 0u;
-    const double dV = a.hx * a.hy * a.hz;
+    // nz = 1 is a 2D field in the xy plane: cell area hx hy and no z kinetic term
+    // (every point has k = 0 there, so z = 0 and V has no z part already)
+    const bool two_d = nz == 1;
+    const double dV = a.hx * a.hy * (two_d ? 1.0 : a.hz);
     const double norm = tot[0] * dV;
     const double epot = tot[1] * dV;
     const double eint = 0.5 * a.g * tot[2] * dV;
-    const double ekin =
-        0.5 * dV * (tot[3] / (a.hx * a.hx) + tot[4] / (a.hy * a.hy) + tot[5] / (a.hz * a.hz));
+    const double ekin = 0.5 * dV *
+                        (tot[3] / (a.hx * a.hx) + tot[4] / (a.hy * a.hy) +
+                         (two_d ? 0.0 : tot[5] / (a.hz * a.hz)));
     const double x2 = tot[6] * dV / norm, y2 = tot[7] * dV / norm, z2 = tot[8] * dV / norm;
     double* o = a.out;
     o[0] = norm;
@@ -205,9 +209,11 @@ extern "C" int gp_observables_noalloc(const void* psi, int nx, int ny, int nz, l
     gpk::set_thread_error("psi and out must be device pointers");
     return GP_ERR_ARG;
   }
-  if (nx < 1 || ny < 1 || nz < 1 || nx > gpk::kMaxExtent || ny > gpk::kMaxExtent ||
-      nz > gpk::kMaxExtent) {
-    gpk::set_thread_error("grid extents must be within 1..2048 (the limit of this entry point)");
+  // the extents gp_create accepts: 3..2048 per axis, or nz = 1 for a 2D field
+  if (nx < 3 || ny < 3 || (nz < 3 && nz != 1) || nx > gpk::kMaxExtent ||
+      ny > gpk::kMaxExtent || nz > gpk::kMaxExtent) {
+    gpk::set_thread_error(
+        "grid extents must be within 3..2048 (nz = 1: a 2D field), the limit of this entry point");
     return GP_ERR_ARG;
   }
   if (pitch < nx) {
@@ -222,6 +228,7 @@ extern "C" int gp_observables_noalloc(const void* psi, int nx, int ny, int nz, l
     gpk::set_thread_error("is_complex must be 0 or 1");
     return GP_ERR_ARG;
   }
+  if (nz == 1) dz = lambda = 1.0;   // unused by a 2D field
   if (!finite_pos(dx) || !finite_pos(dy) || !finite_pos(dz) || !finite_pos(gamma) ||
       !finite_pos(nu) || !finite_pos(lambda) || !(g == g)) {
     gpk::set_thread_error("spacings and trap ratios must be finite and > 0, g finite");
