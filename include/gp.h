@@ -212,6 +212,18 @@ int gp_density2d(gp_solver* s, int plane, double* out);
  * check (GP_ERR_NONFINITE, GP_ERR_TIMEOUT), clearing it.                         */
 int gp_sync(gp_solver* s);
 
+/* Limit of the first bounded wait of a sweep kernel on each of its own shared-memory
+ * copies (tile loads, row copies), in nanoseconds.  Default and maximum 2e9 (2 s);
+ * first_wait_ns < 0 restores the default; 0 tests the copy once and gives up at once
+ * if it has not landed.  A wait that gives up sets the solver's timeout status, and
+ * the kernel then waits (up to 2 s, whatever this limit) for the copies it still has
+ * in flight before its blocks exit, so the device stays usable; the next gp_sync
+ * returns GP_ERR_TIMEOUT and clears the status.  Meant for failure-detection tests:
+ * a step whose waits gave up leaves the field partly updated.  Drops the solver's
+ * step graphs (they hold the limit by value).  The paper has no counterpart: this
+ * is failure detection of the GPU path.                                            */
+int gp_set_wait_limit(gp_solver* s, long long first_wait_ns);
+
 /* Per-sweep timing.  While enabled, every x / y / z sweep launch is bracketed by
  * CUDA events on the solver's stream.  gp_get_timing synchronises, adds the
  * elapsed milliseconds of the launches since the last read into ms[0..2] (x, y, z

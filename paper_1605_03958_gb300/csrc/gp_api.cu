@@ -426,6 +426,7 @@ void fill_sweep_params(gp_solver* s) {
       q.counter = s->counters;
       q.scale_out = s->scale;
       q.status = s->status;
+      q.wait_ns = gpk::kWaitLimitNs;
       q.dV = p.dx * p.dy * p.dz;
       q.ntiles = s->L.ntiles_z[m];
       q.trunc = s->trunc[m][a];
@@ -1261,6 +1262,18 @@ int gp_set_g(gp_solver* s, double g) {
       s->sp[m][a].g = g;
       s->sp[m][a].band_dtg = (float)(s->sp[m][a].dt * g);
     }
+  drop_step_graphs(s);   // they hold the old parameters
+  return GP_OK;
+}
+
+int gp_set_wait_limit(gp_solver* s, long long first_wait_ns) {
+  if (!s) return GP_ERR_ARG;
+  const unsigned long long ns =
+      first_wait_ns < 0 ? gpk::kWaitLimitNs
+                        : std::min<unsigned long long>((unsigned long long)first_wait_ns,
+                                                       gpk::kWaitLimitNs);
+  for (int m = 0; m < 2; ++m)
+    for (int a = 0; a < 3; ++a) s->sp[m][a].wait_ns = ns;
   drop_step_graphs(s);   // they hold the old parameters
   return GP_OK;
 }

@@ -410,6 +410,7 @@ int launch_step(gp_pool* P) {
       b.group_max = P->x_group_max[m];
       b.slot_elems = P->slot_elems[m];
       b.status = P->d_status;
+      b.wait_ns = gpk::kWaitLimitNs;
       const int grid = a == 0 ? (b.nitems + gpk::kBatchXWarps - 1) / gpk::kBatchXWarps : b.nitems;
       const cudaError_t e = gpk::launch_batch_sweep(a, P->wl[m][a], b, m == 1, grid,
                                                     a == 0 ? P->x_smem[m] : 0, P->stream);

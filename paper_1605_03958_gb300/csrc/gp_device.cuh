@@ -42,15 +42,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
+// Non-blocking test of phase `parity` of `bar`.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// Wait for phase `parity` of `bar`, giving up after `limit_ns` of wall time.
+// Wait for phase `parity` of `bar`, giving up after `limit_ns` of wall time; a
+// limit of 0 tests the phase once without waiting.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns) {
+  if (limit_ns == 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
@@ -140,10 +155,11 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
 
-// Wait for the tile's load; on timeout flag it, then wait once more (bounded) so
-// that no copy is left writing into shared memory after the block exits.
-__device__ __forceinline__ bool wait_tile(uint64_t* bar, int* status) {
-  if (mbar_wait_bounded(bar, 0, kWaitLimitNs)) return true;
+// Wait for the tile's load (at most first_ns); on timeout flag it, then wait once
+// more (at most kWaitLimitNs) so that no copy is left writing into shared memory
+// after the block exits.
+__device__ __forceinline__ bool wait_tile(uint64_t* bar, int* status, uint64_t first_ns) {
+  if (mbar_wait_bounded(bar, 0, first_ns)) return true;
   if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
   mbar_wait_bounded(bar, 0, kWaitLimitNs);
   return false;

@@ -16,7 +16,11 @@ namespace gpk {
 constexpr int kStatusNonFinite = 1;  // norm non-finite or zero (imaginary time)
 constexpr int kStatusTimeout = 2;    // a bounded wait on a tile copy ran out
 
-// Bounded waits on a block's own copies give up after this much wall time.
+// Bounded waits on a block's own copies give up after this much wall time.  A
+// solver's first wait on each copy takes its own limit (SweepParams::wait_ns, this
+// value unless gp_set_wait_limit changed it); the wait that drains the copies still
+// in flight after a timeout always takes this one, so that no copy is left writing
+// into shared memory after the block exits.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // Largest grid extent per axis accepted by the ABI.
@@ -85,6 +89,7 @@ struct SweepParams {
   int* status;
   double dV;
   long long ntiles;
+  unsigned long long wait_ns;   // limit of the first bounded wait on each copy
 };
 
 // One resident solve of a pool (gp_batch.cu), as the batched FP32 sweeps see it.
@@ -128,6 +133,7 @@ struct BatchArgs {
   int group_max;          // x: row slots per stage (the largest group of the items)
   int slot_elems;         // x: shared-memory row slot, elements (>= pitch + 16 of every slot)
   int* status;
+  unsigned long long wait_ns;   // limit of the first bounded wait on each copy
 };
 
 // Arguments of the reductions and conversion kernels.

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
     bulk_load(tile, gtile, bytes, bar);
   }
   __syncwarp();
-  if (!wait_tile(bar, p.status)) return;
+  if (!wait_tile(bar, p.status, p.wait_ns)) return;
 
   if (lane < rows) {
     const long long r = r0 + lane;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(32) k_sweep_y(const __grid_constant__ CUtensor
       tma_load_3d(smem + c * box_bytes, &map, cx, c * p.box, k, bar);
   }
   __syncwarp();
-  if (!wait_tile(bar, p.status)) return;
+  if (!wait_tile(bar, p.status, p.wait_ns)) return;
   solve_columns<R, CPLX, false>(tile, W, p.n, static_cast<const E*>(p.A),
                                 static_cast<const E*>(p.B), p.head);
   fence_smem_to_async();
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(32) k_sweep_z(const __grid_constant__ CUtensor
   }
   __syncwarp();
   double acc = 0.0;
-  if (wait_tile(bar, p.status)) {
+  if (wait_tile(bar, p.status, p.wait_ns)) {
     acc = solve_columns<R, CPLX, NORM>(tile, W, p.n, static_cast<const E*>(p.A),
                                        static_cast<const E*>(p.B), p.head);
     fence_smem_to_async();
@@ -749,6 +749,7 @@ template <class E> struct XRows {
   const E* wt;           // w_{k-W}, k = 0 .. 2W (centre as w_0 - 1)
   const double* scale;   // pending renormalisation factor
   int* status;
+  unsigned long long wait_ns;   // limit of the first bounded wait on each row copy
   long long row0;
   int nrow, nx, pitch, S, G, slot_elems;
   int pw;                // 1: pointwise substep on load; 0: only the pending factor
@@ -812,7 +813,7 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
     const int nv = rows * nvec;            // vectors of the group
     const long long gr0 = row0 + (long long)i * G;
     const E fnext = (i + 1 < ngroups && lane < min(G, nrow - (i + 1) * G)) ? fyz[gr0 + G + lane] : F::zero();
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], phase, kWaitLimitNs))) {
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], phase, a.wait_ns))) {
       if (lane == 0) {
         atomicOr(a.status, kStatusTimeout);
         // wait (bounded) for every copy still in flight before the warp exits
@@ -1010,7 +1011,7 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
     E* row = slots + (size_t)st * se;
     const E fr = f_next;
     if (i + 1 < nrow) f_next = fyz[i + 1];
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], phase, kWaitLimitNs))) {
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], phase, a.wait_ns))) {
       if (lane == 0) {
         atomicOr(a.status, kStatusTimeout);
         // wait (bounded) for every copy still in flight before the warp exits
@@ -1077,6 +1078,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.wt = reinterpret_cast<const E*>(p.band_wt);
   a.scale = p.scale;
   a.status = p.status;
+  a.wait_ns = p.wait_ns;
   a.row0 = row0;
   a.nrow = nrow;
   a.nx = p.nx;
@@ -1114,6 +1116,7 @@ __global__ void __launch_bounds__(32 * kBatchXWarps) k_batch_x_band(const __grid
   a.wt = reinterpret_cast<const E*>(d.wt[0]) + (kBandHalfMax - W);
   a.scale = d.scale;
   a.status = b.status;
+  a.wait_ns = b.wait_ns;
   a.row0 = it.row0;
   a.nrow = it.nrow;
   a.nx = d.nx;

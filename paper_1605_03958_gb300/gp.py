@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_density1d": (i, [vp, i, dp]),
         "gp_density2d": (i, [vp, i, dp]),
         "gp_sync": (i, [vp]),
+        "gp_set_wait_limit": (i, [vp, ctypes.c_longlong]),
         "gp_set_timing": (i, [vp, i]),
         "gp_get_timing": (i, [vp, dp, ctypes.POINTER(ll)]),
         "gp_get_info": (i, [vp, ctypes.POINTER(ll)]),
@@ -275,6 +276,10 @@ def gp_density2d(h, plane: int, shape) -> np.ndarray:
 
 def gp_sync(h) -> None:
     _check(load_library().gp_sync(h), h)
+
+
+def gp_set_wait_limit(h, first_wait_ns: int) -> None:
+    _check(load_library().gp_set_wait_limit(h, int(first_wait_ns)), h)
 
 
 def gp_set_timing(h, enable: bool) -> None:
