@@ -214,8 +214,7 @@ int gp_sync(gp_solver* s);
 
 /* Limit of the first bounded wait of a sweep kernel on each of its own shared-memory
  * copies (tile loads, row copies), in nanoseconds.  Default and maximum 2e9 (2 s);
- * first_wait_ns < 0 restores the default; 0 tests the copy once and gives up at once
- * if it has not landed.  A wait that gives up sets the solver's timeout status, and
+ * first_wait_ns < 0 restores the default; 0 makes every first wait give up at once.  A wait that gives up sets the solver's timeout status, and
  * the kernel then waits (up to 2 s, whatever this limit) for the copies it still has
  * in flight before its blocks exit, so the device stays usable; the next gp_sync
  * returns GP_ERR_TIMEOUT and clears the status.  Meant for failure-detection tests:
@@ -238,7 +237,8 @@ int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]);
  *   info[6] bit a set when sweep a (0 x, 1 y, 2 z) uses the FP32 kernels without
  *           shared-memory line tiles (decaying coupling cut below FP32 rounding, see
  *           gp_sweeps.cu), bit 3 + a when that kernel is the banded operator, bits
- *           8..11 the largest band half-width W,
+ *           8..11 the largest band half-width W, bits 12 + a when sweep a uses the
+ *           FP64 line-streaming kernels (FP64 field; gp_sweeps64.cu),
  *   info[7] the truncation depth L of the streaming recurrences (0 when none).
  * GP_SWEEP_KERNELS=tile in the environment at gp_create time makes every sweep
  * use the tile kernels; =stream keeps the FP32 sweeps on the streaming recurrences

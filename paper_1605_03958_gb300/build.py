@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgp_sscn.so")
-SOURCES = ["gp_api.cu", "gp_sweeps.cu", "gp_reduce.cu", "gp_noalloc.cu", "gp_batch.cu"]
+SOURCES = ["gp_api.cu", "gp_sweeps.cu", "gp_sweeps64.cu", "gp_reduce.cu", "gp_noalloc.cu",
+           "gp_batch.cu"]
 HEADERS = ["gp_device.cuh", "gp_internal.h", "gp_arena.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

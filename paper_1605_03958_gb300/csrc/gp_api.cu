@@ -243,6 +243,12 @@ bool force_tile() {
   const char* v = std::getenv("GP_SWEEP_KERNELS");
   return v && std::strcmp(v, "tile") == 0;
 }
+// GP_BAND_PREFETCH=0 keeps the banded y / z sweeps' turn loads in registers instead
+// of copying them to shared memory one turn ahead (A/B measurements).
+bool band_prefetch() {
+  const char* v = std::getenv("GP_BAND_PREFETCH");
+  return !(v && std::strcmp(v, "0") == 0);
+}
 bool force_stream() {
   const char* v = std::getenv("GP_SWEEP_KERNELS");
   return v && (std::strcmp(v, "stream") == 0 || std::strcmp(v, "stream_x") == 0);
@@ -297,6 +303,7 @@ struct gp_solver {
   int trunc[2][3] = {};              // FP32 fast sweeps: truncation depth, 0 = use the tile kernel
   int fast_grid[2][3] = {};          // blocks of the fast sweeps (x band: persistent grid)
   int band_w[2][3] = {};             // FP32 banded sweep half-width per mode and axis, 0 = not used
+  bool line64 = false;               // FP64 field: the line-streaming sweeps of gp_sweeps64.cu
   int split = GP_SPLIT_LIE;          // splitting of a step
   bool kinetic_only = false;         // x sweep without the pointwise substep (Strang)
   float band_wt[2][3][2 * 17] = {};  // its weights (complex: pairs)
@@ -507,7 +514,8 @@ void fill_sweep_params(gp_solver* s) {
         const int P = 2 * q.band_w + 1;
         const int ept = m == 0 ? 4 : 2;
         const long long cols = (long long)((p.nx + ept - 1) / ept) * (a == 1 ? p.nz : p.ny);
-        const int bps = std::max(1, gpk::band_line_blocks_per_sm(a, m == 1, q.band_w));
+        q.band_cp = band_prefetch() ? 1 : 0;
+        const int bps = std::max(1, gpk::band_line_blocks_per_sm(a, m == 1, q.band_w, q.band_cp != 0));
         const long long cap = (long long)s->nsm * bps * 128;
         int best_seg = P;
         double best = -1.0;
@@ -769,6 +777,16 @@ int create_impl(const gp_params* p, void* dev_buf, size_t bytes, void* stream, g
     return bail(GP_ERR_CUDA);
   }
   if ((rc = encode_maps(s)) != GP_OK) return bail(rc);
+  // FP64 fields use the line-streaming sweeps unless the tile kernels are forced;
+  // the z sweep's norm takes one partial per block
+  if (L.rbytes == 8 && !force_tile() &&
+      gpk::sweep64_blocks(2, p->nx, p->ny, p->nz) <= (long long)L.npartials) {
+    if ((e = gpk::sweep64_prepare()) != cudaSuccess) {
+      cuda_fail(s, e, "cudaFuncSetAttribute");
+      return bail(GP_ERR_CUDA);
+    }
+    s->line64 = true;
+  }
   fill_sweep_params(s);
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) {
     cuda_fail(s, e, "cudaStreamSynchronize");
@@ -807,6 +825,8 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
     e = gpk::launch_sweep_band_line(axis, q, m == 1, s->fast_grid[m][axis], s->stream);
   else if (q.trunc)
     e = gpk::launch_sweep_fast(axis, q, m == 1, s->fast_grid[m][axis], s->stream);
+  else if (s->line64)
+    e = gpk::launch_sweep64(axis, q, m == 1, s->stream);
   else if (axis == 0)
     e = gpk::launch_sweep_x<R>(q, m == 1, smem, s->stream);
   else if (axis == 1)
@@ -1392,6 +1412,7 @@ int gp_get_info(const gp_solver* s, long long info[8]) {
     wmax = std::max(wmax, s->band_w[m][a]);
   }
   info[6] |= (long long)wmax << 8;
+  if (s->line64) info[6] |= 7LL << 12;
   info[7] = std::max(s->trunc[m][0], std::max(s->trunc[m][1], s->trunc[m][2]));
   return GP_OK;
 }

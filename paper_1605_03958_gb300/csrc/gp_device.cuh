@@ -42,19 +42,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Non-blocking test of phase `parity` of `bar`.
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -62,10 +49,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wait for phase `parity` of `bar`, giving up after `limit_ns` of wall time; a
-// limit of 0 tests the phase once without waiting.
+// limit of 0 gives up at once (failure-detection tests).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns) {
-  if (limit_ns == 0) return mbar_test_wait(bar, parity);
+  if (limit_ns == 0) return false;
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
@@ -135,6 +122,14 @@ __device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, bool 
                "n"(BYTES), "r"(n)
                : "memory");
 }
+// 16-byte asynchronous global -> shared copy cached in L2 only; fills zeros when !valid
+// (src must still be a valid address).
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
+  const uint32_t n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(n)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -163,6 +158,65 @@ __device__ __forceinline__ bool wait_tile(uint64_t* bar, int* status, uint64_t f
   if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
   mbar_wait_bounded(bar, 0, kWaitLimitNs);
   return false;
+}
+
+// ----------------------------------------------------- fused norm reduction
+
+// Fixed-order block reduction of one FP64 value per warp into partials[block];
+// the last block to finish sums the partials and writes the renormalisation factor.
+// Every thread of the block must call it.  The last block's work is the kernel's
+// tail (FP64 is narrow on this part: every dependent FP64 operation costs about a
+// warp's worth of pipe cycles), so its sums are shallow pairwise trees in a fixed
+// order: four partials per thread loaded together, (x0 + x1) + (x2 + x3), the warp
+// shuffle tree, the warps' sums pairwise; the factor is rsqrt(norm), like
+// 1 / sqrt(norm) within 1 ulp of the exact value.
+__device__ __forceinline__ double sum_fixed(const double* w, int n) {
+  if (n == 4) return (w[0] + w[1]) + (w[2] + w[3]);
+  double v = w[0];
+  for (int i = 1; i < n; ++i) v += w[i];
+  return v;
+}
+__device__ __forceinline__ void norm_finish(double acc, double* partials, unsigned int* counter,
+                                            unsigned int nb, unsigned int bid, double* scale_out,
+                                            int* status, double dV) {
+  __shared__ double wpart[32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) wpart[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    partials[bid] = sum_fixed(wpart, nw);
+    // release of this block's partial and, for the last block, acquire of all the
+    // others' (the counter's atomic updates form one release sequence); the block's
+    // barrier then orders its threads' loads after the acquire
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(counter) : "memory");
+    last = (old == nb - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  const unsigned int T = blockDim.x;
+  auto quad = [&](unsigned int t0) {
+    double x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const unsigned int t = t0 + q * T;
+      x[q] = t < nb ? __ldcg(partials + t) : 0.0;
+    }
+    return (x[0] + x[1]) + (x[2] + x[3]);
+  };
+  double s = quad(threadIdx.x);
+  for (unsigned int t0 = threadIdx.x + 4 * T; t0 < nb; t0 += 4 * T) s += quad(t0);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) wpart[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double norm = sum_fixed(wpart, nw) * dV;
+    if (!(norm > 0.0) || !isfinite(norm)) atomicOr(status, kStatusNonFinite);
+    *scale_out = rsqrt(norm);
+    *counter = 0u;
+  }
 }
 
 // ------------------------------------------------------------------- arithmetic

@@ -74,6 +74,7 @@ struct SweepParams {
   int band_stages;       // x: groups of rows in flight per warp
   int band_group;        // x: rows per group (worked on together by the warp's lanes)
   int band_seg;          // y / z: points per line segment (a multiple of 2 band_w + 1)
+  int band_cp;           // y / z: 1 = next turn's inputs copied to shared memory ahead (cp.async)
   float band_dtg;        // x: dt g in FP32
   // pointwise substep (x sweep only)
   int pw;                // 1: pointwise substep fused on load; 0: kinetic-only step
@@ -171,7 +172,7 @@ cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int gr
 // FP32 banded y / z sweeps (out of place like the streaming ones), blocks of 128 threads.
 cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_field, int grid,
                                    cudaStream_t st);
-int band_line_blocks_per_sm(int axis, bool complex_field, int w);
+int band_line_blocks_per_sm(int axis, bool complex_field, int w, bool cp);
 // Batched FP32 banded sweeps over the slots of a pool (one launch per direction
 // and mode): x on kBandWarps-warp blocks with dynamic shared memory
 // batch_x_smem(); y / z on blocks of 128 threads.  w is the launch half-width.
@@ -182,6 +183,14 @@ int x_band_group(int nx, int ept, int stages, size_t slot_bytes, size_t warp_bud
 cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_blocks_per_sm);
 cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,
                                size_t smem, cudaStream_t st);
+// FP64 sweeps (gp_sweeps64.cu): x moves 32 rows per warp through shared-memory
+// chunks (dynamic shared memory x64_smem), y / z stream one line per thread; the
+// launch covers the whole grid (sweep64_blocks blocks).  sweep64_prepare sets the x
+// kernels' shared-memory limit (once per device).
+size_t x64_smem(bool complex_field);
+cudaError_t sweep64_prepare();
+long long sweep64_blocks(int axis, int nx, int ny, int nz);
+cudaError_t launch_sweep64(int axis, const SweepParams& p, bool complex_field, cudaStream_t st);
 // Resident warps per SM of the streaming y / z kernel (occupancy calculator).
 int stream_warps_per_sm(int axis, bool complex_field, int trunc);
 

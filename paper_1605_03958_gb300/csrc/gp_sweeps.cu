@@ -368,62 +368,6 @@ __global__ void __launch_bounds__(32) k_sweep_z(const __grid_constant__ CUtensor
 constexpr int kStreamU = GP_STREAM_U;  // chunk length of the streaming kernel (load lead)
 constexpr int kHeadMax = 8;     // largest `head` the streaming kernel handles
 
-// Fixed-order block reduction of one FP64 value per warp into partials[block];
-// the last block to finish sums the partials and writes the renormalisation factor.
-// Every thread of the block must call it.  The last block's work is the kernel's
-// tail (FP64 is narrow on this part: every dependent FP64 operation costs about a
-// warp's worth of pipe cycles), so its sums are shallow pairwise trees in a fixed
-// order: four partials per thread loaded together, (x0 + x1) + (x2 + x3), the warp
-// shuffle tree, the warps' sums pairwise; the factor is rsqrt(norm), like
-// 1 / sqrt(norm) within 1 ulp of the exact value.
-__device__ __forceinline__ double sum_fixed(const double* w, int n) {
-  if (n == 4) return (w[0] + w[1]) + (w[2] + w[3]);
-  double v = w[0];
-  for (int i = 1; i < n; ++i) v += w[i];
-  return v;
-}
-__device__ __forceinline__ void norm_finish(double acc, double* partials, unsigned int* counter,
-                                            unsigned int nb, unsigned int bid, double* scale_out,
-                                            int* status, double dV) {
-  __shared__ double wpart[32];
-  __shared__ int last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) wpart[warp] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    partials[bid] = sum_fixed(wpart, nw);
-    // release of this block's partial and, for the last block, acquire of all the
-    // others' (the counter's atomic updates form one release sequence); the block's
-    // barrier then orders its threads' loads after the acquire
-    unsigned int old;
-    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(counter) : "memory");
-    last = (old == nb - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  const unsigned int T = blockDim.x;
-  auto quad = [&](unsigned int t0) {
-    double x[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const unsigned int t = t0 + q * T;
-      x[q] = t < nb ? __ldcg(partials + t) : 0.0;
-    }
-    return (x[0] + x[1]) + (x[2] + x[3]);
-  };
-  double s = quad(threadIdx.x);
-  for (unsigned int t0 = threadIdx.x + 4 * T; t0 < nb; t0 += 4 * T) s += quad(t0);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) wpart[warp] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const double norm = sum_fixed(wpart, nw) * dV;
-    if (!(norm > 0.0) || !isfinite(norm)) atomicOr(status, kStatusNonFinite);
-    *scale_out = rsqrt(norm);
-    *counter = 0u;
-  }
-}
 __device__ __forceinline__ void norm_block_finish(double acc, const SweepParams& p) {
   norm_finish(acc, p.partials, p.counter, gridDim.x, blockIdx.x, p.scale_out, p.status, p.dV);
 }
@@ -1231,7 +1175,119 @@ __device__ __forceinline__ double band_line_thread(const LineArgs<typename Field
   return acc;
 }
 
+
+// The same segment with the turn's P new inputs copied to shared memory one turn
+// ahead (cp.async, 16 bytes per input): the copies of turn b + 1 are in flight while
+// turn b is computed, and they hold no registers, so the kernel keeps more warps
+// resident than the register form above.  `slots` is the block's [2][P][blockDim]
+// array of 16-byte slots; a thread uses only its own.  The odd images past the
+// line's ends are copied from their mirror positions and negated when read.
 template <class R, bool CPLX, int AXIS, bool NORM, int W>
+__device__ __forceinline__ double band_line_thread_cp(const LineArgs<typename Field<R, CPLX>::E>& p,
+                                                      long long t, float4* slots) {
+  using F = Field<R, CPLX>;
+  using E = typename F::E;
+  constexpr int EPT = 16 / (int)sizeof(E);
+  constexpr int P = 2 * W + 1;
+  const int nx = p.nx, n = p.n, Ls = p.Ls;
+  const int nvec = (nx + EPT - 1) / EPT;
+  const int nother = AXIS == 1 ? p.nz : p.ny;
+  const int nseg = (n + Ls - 1) / Ls;
+  const E* wt = p.wt;
+  const int bt = blockDim.x, tid = threadIdx.x;
+  double acc = 0.0;
+  if (t < (long long)nvec * nother * nseg) {
+    const int xv = (int)(t % nvec);
+    const long long rest = t / nvec;
+    const int o = (int)(rest % nother), sg = (int)(rest / nother);
+    const size_t pitch = (size_t)p.pitch;
+    const size_t base = (AXIS == 1 ? (size_t)o * p.ny * pitch : (size_t)o * pitch) + (size_t)xv * EPT;
+    const float4* in = reinterpret_cast<const float4*>(p.psi + base);
+    float4* out = reinterpret_cast<float4*>(p.out + base);
+    const size_t sv = (AXIS == 1 ? pitch : pitch * p.ny) * sizeof(E) / 16;   // line stride in vectors
+    const int valid = min(EPT, nx - xv * EPT);   // elements of this vector inside the field
+    const int j0 = sg * Ls, j1 = min(n, j0 + Ls);
+    const bool interior = j0 >= W && j0 + Ls + W <= n;
+    // input j of the odd extension about the ghosts -1 and n
+    auto ld = [&](int j) -> float4 {
+      if (interior || (j >= 0 && j < n)) return in[(size_t)j * sv];
+      if (j == -1 || j == n) return make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = in[(size_t)(j < 0 ? -2 - j : 2 * n - j) * sv];
+      return make_float4(-v.x, -v.y, -v.z, -v.w);
+    };
+    // copy of turn b's inputs j = b + u + W (u < P) into slot set h
+    auto issue = [&](int b, int h) {
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int j = b + u + W;
+        int src = j;
+        bool ok = true;
+        if (!interior) {
+          ok = b + u < j1 && j != -1 && j != n;
+          src = j < 0 ? -2 - j : (j > n ? 2 * n - j : j);
+          if (!ok) src = 0;
+        }
+        cp_async16_zfill(slots + (size_t)(h * P + u) * bt + tid, in + (size_t)src * sv, ok);
+      }
+    };
+    float4 ring[P];
+#pragma unroll
+    for (int m = 0; m < 2 * W; ++m) ring[m] = ld(j0 - W + m);
+    issue(j0, 0);
+    cp_async_commit();
+    int h = 0;
+    for (int b = j0; b < j1; b += P, h ^= 1) {
+      if (b + P < j1) issue(b + P, h ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();   // turn b's copies have landed
+      float part = 0.f;
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int j = b + u;
+        if (interior || j < j1) {
+          float4 v = slots[(size_t)(h * P + u) * bt + tid];
+          if (!interior) {
+            const int jj = j + W;
+            if (jj < -1 || jj > n) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+          }
+          ring[(u + 2 * W) % P] = v;
+          const E* c = reinterpret_cast<const E*>(&ring[(u + W) % P]);
+          float4 ov;
+          E* oe = reinterpret_cast<E*>(&ov);
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            E a = F::mul(wt[W], c[e]);
+#pragma unroll
+            for (int k = 1; k <= W; ++k) {
+              const E* lo = reinterpret_cast<const E*>(&ring[(u + W - k) % P]);
+              const E* hi = reinterpret_cast<const E*>(&ring[(u + W + k) % P]);
+              a = F::chain(wt[W + k], F::add(lo[e], hi[e]), a);
+            }
+            oe[e] = F::add(c[e], a);
+          }
+          if (valid == EPT) {
+            out[(size_t)j * sv] = ov;
+            if (NORM) {
+#pragma unroll
+              for (int e = 0; e < EPT; ++e) part += F::abs2(oe[e]);
+            }
+          } else {
+            E* os = reinterpret_cast<E*>(out + (size_t)j * sv);
+            for (int e = 0; e < valid; ++e) {
+              os[e] = oe[e];
+              if (NORM) part += F::abs2(oe[e]);
+            }
+          }
+        }
+      }
+      if (NORM) acc += (double)part;
+    }
+    cp_async_wait<0>();
+  }
+  return acc;
+}
+
+template <class R, bool CPLX, int AXIS, bool NORM, int W, bool CP>
 __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__ SweepParams p) {
   pdl_begin();
   using E = typename Field<R, CPLX>::E;
@@ -1245,7 +1301,14 @@ __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__
   a.n = p.n;
   a.pitch = p.pitch;
   a.Ls = p.band_seg;
-  const double acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc;
+  if constexpr (CP) {
+    extern __shared__ __align__(16) float4 band_slots[];
+    acc = band_line_thread_cp<R, CPLX, AXIS, NORM, W>(a, t, band_slots);
+  } else {
+    acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, t);
+  }
   if (NORM) norm_block_finish(acc, p);
 }
 
@@ -1410,33 +1473,42 @@ cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int gr
   return launch_pdl(k, grid, 32 * kBandWarps, x_band_smem(p, complex_field), st, p);
 }
 
+// shared memory of a banded y / z block: 128 threads x two turns of 2W+1 16-byte slots
+static size_t band_line_smem(int W, bool cp) { return cp ? (size_t)128 * 2 * (2 * W + 1) * 16 : 0; }
+
+using SweepKernel = void (*)(SweepParams);
+template <int W, bool CP> static SweepKernel band_line_kernel(int axis, bool cplx) {
+  if (axis == 1)
+    return cplx ? k_sweep_band_line<float, true, 1, false, W, CP> : k_sweep_band_line<float, false, 1, false, W, CP>;
+  return cplx ? k_sweep_band_line<float, true, 2, false, W, CP> : k_sweep_band_line<float, false, 2, true, W, CP>;
+}
+
 template <int W>
 static cudaError_t launch_band_line_W(int axis, const SweepParams& p, bool cplx, int grid,
                                      cudaStream_t st) {
-  if (axis == 1)
-    return cplx ? launch_pdl(k_sweep_band_line<float, true, 1, false, W>, grid, 128, 0, st, p)
-                : launch_pdl(k_sweep_band_line<float, false, 1, false, W>, grid, 128, 0, st, p);
-  return cplx ? launch_pdl(k_sweep_band_line<float, true, 2, false, W>, grid, 128, 0, st, p)
-              : launch_pdl(k_sweep_band_line<float, false, 2, true, W>, grid, 128, 0, st, p);
+  const bool cp = p.band_cp != 0;
+  void (*k)(SweepParams) = cp ? band_line_kernel<W, true>(axis, cplx) : band_line_kernel<W, false>(axis, cplx);
+  return launch_pdl(k, grid, 128, band_line_smem(W, cp), st, p);
 }
 
-template <int W> static int band_line_blocks_per_sm_W(int axis, bool cplx) {
-  int b = 0;
-  if (axis == 1) {
-    if (cplx) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, true, 1, false, W>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, false, 1, false, W>, 128, 0);
-  } else {
-    if (cplx) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, true, 2, false, W>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_band_line<float, false, 2, true, W>, 128, 0);
+template <int W> static int band_line_blocks_per_sm_W(int axis, bool cplx, bool cp) {
+  void (*k)(SweepParams) = cp ? band_line_kernel<W, true>(axis, cplx) : band_line_kernel<W, false>(axis, cplx);
+  const size_t smem = band_line_smem(W, cp);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 128, smem);
   return b;
 }
 
-int band_line_blocks_per_sm(int axis, bool complex_field, int w) {
+int band_line_blocks_per_sm(int axis, bool complex_field, int w, bool cp) {
   switch (w) {
-    case 3: return band_line_blocks_per_sm_W<3>(axis, complex_field);
-    case 5: return band_line_blocks_per_sm_W<5>(axis, complex_field);
-    case 8: return band_line_blocks_per_sm_W<8>(axis, complex_field);
+    case 3: return band_line_blocks_per_sm_W<3>(axis, complex_field, cp);
+    case 5: return band_line_blocks_per_sm_W<5>(axis, complex_field, cp);
+    case 8: return band_line_blocks_per_sm_W<8>(axis, complex_field, cp);
     default: return 0;
   }
 }

@@ -301,6 +301,7 @@ def gp_get_info(h) -> dict:
     d = dict(zip(keys, list(v)))
     d["band_mask"] = (d["fast_mask"] >> 3) & 7
     d["band_w"] = (d["fast_mask"] >> 8) & 15
+    d["line64_mask"] = (d["fast_mask"] >> 12) & 7
     d["fast_mask"] &= 7
     return d
 

@@ -38,6 +38,8 @@ def solver(P, p, prec="f64", use_torch=True):
 
 
 def rel(a, b):
+    if b == 0:   # e.g. rms_z of a 2D field: exactly zero on both sides
+        return abs(a)
     return abs(a - b) / abs(b)
 
 
@@ -443,3 +445,49 @@ def test_fp32_overlapped_read_equals_synchronous_read(P, orc, mode, nx):
         P.gp.gp_get_psi_f32_async_ptr(a.handle, host.data_ptr(), not cplx)
     for s in (a, b):
         s.close()
+
+
+# ------------------------------------------- FP64 line-streaming vs tile kernels
+
+F64_SHAPES = [(240, 40, 32), (37, 29, 23), (70, 9, 37), (3, 70, 41), (33, 65, 5), (300, 7, 3),
+              (48, 40, 1)]
+
+
+@pytest.mark.parametrize("shape", F64_SHAPES)
+@pytest.mark.parametrize("mode", ["imag", "real"])
+@pytest.mark.parametrize("g", [40.0, 3000.0])
+def test_fp64_line_kernels_match_tile_kernels_and_oracle(P, orc, shape, mode, g, monkeypatch):
+    """The FP64 line-streaming sweeps (x in 32-row warps through shared-memory chunks,
+    y / z one line per thread; the exp / cis polynomial's degree picked from a bound on
+    its argument) against the FP64 tile kernels and the oracle, on ragged chunks and
+    row counts, a 2D grid, a small nonlinear phase (g = 40: the lowest-degree
+    polynomials) and a large one (g = 3000: the higher degrees and library branch)."""
+    p = problem(orc, *shape, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=g, hy=0.18, hz=0.22)
+    steps = 12
+    if mode == "imag":
+        psi0 = orc.init_gaussian(p)
+        ref = orc.step_imag(p, psi0, steps)
+    else:
+        psi0 = orc.step_imag(p, orc.init_gaussian(p), 10).astype(complex)
+        ref = orc.step_real(p, psi0, steps)
+    outs = {}
+    for kind in ("auto", "tile"):
+        if kind == "auto":
+            monkeypatch.delenv("GP_SWEEP_KERNELS", raising=False)
+        else:
+            monkeypatch.setenv("GP_SWEEP_KERNELS", kind)
+        s = solver(P, p)
+        s.set_psi(psi0)
+        if mode == "imag":
+            s.step_imag(steps)
+        else:
+            s.step_real(steps)
+        outs[kind] = (s.get_psi(as_complex=mode == "real"), s.info(), s.observables())
+        s.close()
+    monkeypatch.delenv("GP_SWEEP_KERNELS", raising=False)
+    assert outs["auto"][1]["line64_mask"] == 7
+    assert outs["tile"][1]["line64_mask"] == 0
+    scale = max(1.0, np.max(np.abs(ref)))
+    for kind in outs:
+        assert np.max(np.abs(outs[kind][0] - ref)) <= PSI_TOL * scale, kind
+    assert_obs_close(outs["auto"][2], orc.observables(p, ref), MU_TOL, 1e-12)

@@ -3,9 +3,8 @@
 Each sweep kernel waits on its own shared-memory copies (row copies of the x sweeps,
 tile loads of the FP64 sweeps) with a bounded wait that, when it gives up, sets the
 solver's timeout status, drains the copies still in flight (up to 2 s) and lets its
-blocks exit.  gp_set_wait_limit(s, 0) makes the first wait on each copy test it once
-and give up if it has not landed, which is certain for the first copy of every warp
-or block (it was issued a few instructions earlier).  Nothing faults: the host sees
+blocks exit.  gp_set_wait_limit(s, 0) makes the first wait on each copy give up at
+once, so every warp or block takes that path.  Nothing faults: the host sees
 GP_ERR_TIMEOUT from gp_sync, the status is cleared, and the next steps on the same
 solver (limit restored) give the same bits as a solver that never timed out.
 """
@@ -27,13 +26,17 @@ def P():
 
 
 # x rows of 60 (one row per warp at a time) and 16 (grouped rows) 16-byte vectors in
-# FP32; FP64 runs the tile kernels (bulk row tiles along x, TMA tiles along y and z)
+# FP32 (banded x sweep); the tile kernels (bulk row tiles along x, TMA tiles along y
+# and z), which FP64 solvers run when GP_SWEEP_KERNELS=tile (their default kernels
+# stream lines through global memory and have no waits)
 CASES = [("f32", (240, 40, 32)), ("f32", (64, 40, 32)), ("f64", (64, 48, 32))]
 
 
 @pytest.mark.parametrize("prec,shape", CASES)
 @pytest.mark.parametrize("mode", ["imag", "real"])
-def test_wait_that_runs_out_is_reported_and_the_solver_recovers(P, prec, shape, mode):
+def test_wait_that_runs_out_is_reported_and_the_solver_recovers(P, prec, shape, mode, monkeypatch):
+    if prec == "f64":
+        monkeypatch.setenv("GP_SWEEP_KERNELS", "tile")
     nx, ny, nz = shape
     args = (nx, ny, nz, 0.2, 0.2, 0.2, 0.004, 1.0, 1.41, 2.0)
     s = P.Solver(*args, g=50.0, prec=prec)
