@@ -48,7 +48,12 @@ def parse():
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--e2e-steps", type=int, default=50)
-    ap.add_argument("--f64-steps", type=int, default=300)
+    ap.add_argument("--f64-steps", type=int, default=300,
+                    help="context: timed steps of the FP64 imaginary-time solve (complex128 "
+                         "real time: a third of them)")
+    ap.add_argument("--no-context", dest="context", action="store_false",
+                    help="skip the context lines (paper precision, DRAM-bound grid, shortened "
+                         "batched and served workloads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["single", "batch", "serve", "c1"], default="single",
                     help="single: the 240x200x160 solve (default); batch: 64 uneven FP32 "
@@ -194,6 +199,274 @@ def replica_throughput(local_ms, units_per_rank, group=None, device=None):
     return world * units_per_rank / (ms / 1e3), ms
 
 
+# ------------------------------------------------------------ shared helpers
+
+def sweep_kernel_names(info, prec, real):
+    """Kernel (template) names of the x, y, z sweeps a solver with gp_get_info `info` runs."""
+    rt = "float" if prec == "f32" else "double"
+    L = info["trunc"]
+    W = info["band_w"]
+    c = "true" if real else "false"     # complex field
+    nm = "false" if real else "true"    # the z sweep sums the norm in imaginary time only
+    if info.get("line64_mask", 0) == 7:
+        return {"sweep_x": f"k_sweep_x64<{c}>", "sweep_y": f"k_sweep_line64<{c},1,false>",
+                "sweep_z": f"k_sweep_line64<{c},2,{nm}>"}
+    return {
+        "sweep_x": (f"k_sweep_x_band<float,{c},{W}>" if info["band_mask"] & 1 else
+                    f"k_sweep_x_stream<float,{c},{L}>" if info["fast_mask"] & 1 else f"k_sweep_x<{rt},{c}>"),
+        "sweep_y": (f"k_sweep_band_line<float,{c},1,false,{W}>" if info["band_mask"] & 2 else
+                    f"k_sweep_stream<float,{c},1,false,{L}>" if info["fast_mask"] & 2 else f"k_sweep_y<{rt},{c}>"),
+        "sweep_z": (f"k_sweep_band_line<float,{c},2,{nm},{W}>" if info["band_mask"] & 4 else
+                    f"k_sweep_stream<float,{c},2,{nm},{L}>" if info["fast_mask"] & 4 else f"k_sweep_z<{rt},{c},{nm}>")}
+
+
+def make_workload_solver(P, prec, mode, grid, splitting="lie"):
+    """The bench's solve on `grid`: imaginary time (dt = 0.1 h^2, g = 100, from the
+    Gaussian) or the quench (dt = 0.02 h^2: 300 imaginary steps at g = 100, then
+    g = 200 in real time).  Returns (solver, step function)."""
+    real = mode == "real"
+    dt = (0.02 if real else 0.1) * H * H
+    so = P.Solver(*grid, H, dt=dt, gamma=TRAP[0], nu=TRAP[1], lam=TRAP[2], g=G, prec=prec)
+    so.set_splitting(splitting)
+    so.init_gaussian()
+    if real:
+        so.step_imag(300)
+        so.set_g(2 * G)
+    return so, (so.step_real if real else so.step_imag)
+
+
+def time_steps(P, so, step, steps, flush):
+    """Per-step CUDA-event times (L2 flushed between steps, outside the events), then
+    per-sweep times from the library's events over the same number of steps.
+    Returns (ms per step, [avg ms of the x, y, z sweeps], launches per sweep)."""
+    import torch
+    for _ in range(3):
+        step(1)
+        flush()
+    torch.cuda.synchronize()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        e0[k].record()
+        step(1)
+        e1[k].record()
+        flush()
+    torch.cuda.synchronize()
+    ms = sum(e0[k].elapsed_time(e1[k]) for k in range(steps)) / steps
+    P.gp_set_timing(so.handle, True)
+    for _ in range(steps):
+        step(1)
+        flush()
+    kms, kn = P.gp_get_timing(so.handle)
+    P.gp_set_timing(so.handle, False)
+    so.sync()
+    return ms, [kms[i] / max(kn[i], 1) for i in range(3)], kn
+
+
+# FP64 lane operations (DADD, DMUL, DFMA: one each; the FP64 pipe takes them at the
+# same rate) per grid point of each sweep, counted from the arithmetic of the FP64
+# kernels (gp_sweeps64.cu) at the bench workloads: x = pointwise substep (real: 8 at
+# the degree-4 exp polynomial; complex: 21 with the degree-4/5 cos/sin polynomials)
+# + forward (4 / 14) + back substitution (1 / 4); y and z: 5 / 18; the imaginary-time
+# z sweep adds 1 for the norm.
+FP64_OPS = {"imag": (13, 5, 6), "real": (39, 18, 18)}
+
+
+def fp64_peak():
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul, 4096^3, best of 3),
+    as FP64 operations per second (one fused multiply-add = one operation)."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return n ** 3 / (best / 1e3)
+
+
+def fp64_pipe_peak(sm_mhz):
+    """FP64 ALU peak from unit counts and the clock: 2 FP64 lane operations per clock
+    per SM (the rate ncu's sm__inst_executed_pipe_fp64 peak implies on this part, and
+    the nominal 1.25 TFLOP/s at 2.07 GHz over 152 SMs), at the SM clock sampled during
+    the run."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    return 2.0 * nsm * sm_mhz * 1e6, nsm
+
+
+def paper_precision(P, args, flush, hbm, sm_mhz):
+    """FP64 imaginary time on the bench grid and complex128 real time on the quench
+    workload, each with per-sweep times, HBM fractions and FP64 ALU fractions."""
+    grid = (NX, NY, NZ)
+    npts = NX * NY * NZ
+    peak, nsm = fp64_pipe_peak(sm_mhz)
+    out = {"fp64_peak": {"value": round(peak / 1e12, 4), "unit": "T FP64 op/s",
+                         "source": f"derived: 2 FP64 lane op/clk/SM x {nsm} SMs x {sm_mhz:.0f} MHz "
+                                   "(sampled SM clock)",
+                         "dgemm_measured": round(fp64_peak() / 1e12, 4)}}
+    for mode, steps in (("imag", max(args.f64_steps, 3)), ("real", max(args.f64_steps // 3, 3))):
+        so, st = make_workload_solver(P, "f64", mode, grid)
+        ms, sw, kn = time_steps(P, so, st, steps, flush)
+        names = sweep_kernel_names(so.info(), "f64", mode == "real")
+        so.close()
+        ops = FP64_OPS[mode]
+        sb = 16 if mode == "real" else 8
+        per = {}
+        for i, n in enumerate(("sweep_x", "sweep_y", "sweep_z")):
+            achieved = ops[i] * npts / (sw[i] / 1e3)
+            per[n] = {"kernel": names[n], "avg_ms": round(sw[i], 5),
+                      "fp64_ops_per_point": ops[i],
+                      "alu_frac": round(achieved / peak, 3),
+                      "hbm_frac": round(2 * npts * sb / (sw[i] / 1e3) / 1e9 / hbm, 3)}
+        dom = max(per, key=lambda n: per[n]["avg_ms"])
+        out["imag_f64" if mode == "imag" else "real_c128"] = {
+            "workload": (f"imag3d {NX}x{NY}x{NZ}, h=0.1, dt=0.1h^2, trap (1,1.41,2), g=100, "
+                         "imaginary time, FP64 field" if mode == "imag" else
+                         f"real3d {NX}x{NY}x{NZ}, h=0.1, dt=0.02h^2, trap (1,1.41,2), ground state "
+                         "at g=100 then quench to g=200, real time, complex128 field"),
+            "value": round(npts / (ms / 1e3), 1), "unit": "grid-point-steps/s",
+            "ms_per_step": round(ms, 5), "steps": steps, "sweeps": per,
+            "roofline_alu": {"bound": "alu", "kernel": per[dom]["kernel"],
+                             "achieved": round(ops[("sweep_x", "sweep_y", "sweep_z").index(dom)] * npts
+                                               / (per[dom]["avg_ms"] / 1e3) / 1e12, 4),
+                             "peak": round(peak / 1e12, 4), "unit": "T FP64 op/s",
+                             "frac": per[dom]["alu_frac"]}}
+    return out
+
+
+def dram_bound(P, args, flush, hbm):
+    """The same FP32 imaginary-time step on 512 x 400 x 320 (a 262 MB field, twice the
+    L2): every sweep streams from and to DRAM."""
+    grid = (512, 400, 320)
+    npts = grid[0] * grid[1] * grid[2]
+    so, st = make_workload_solver(P, "f32", "imag", grid)
+    ms, sw, kn = time_steps(P, so, st, 20, flush)
+    names = sweep_kernel_names(so.info(), "f32", False)
+    so.close()
+    per = {}
+    for i, n in enumerate(("sweep_x", "sweep_y", "sweep_z")):
+        gbs = 2 * npts * 4 / (sw[i] / 1e3) / 1e9
+        per[n] = {"kernel": names[n], "avg_ms": round(sw[i], 5), "achieved_gbs": round(gbs, 1),
+                  "frac": round(gbs / hbm, 3)}
+    return {"workload": WORKLOAD.replace("240x200x160", "512x400x320"),
+            "value": round(npts / (ms / 1e3), 1), "unit": "grid-point-steps/s",
+            "ms_per_step": round(ms, 5), "steps": 20,
+            "step_frac_of_hbm": round(6 * npts * 4 / (ms / 1e3) / 1e9 / hbm, 3),
+            "sweeps": per, "traffic": ncu_traffic_512()}
+
+
+def ncu_traffic_512():
+    """DRAM bytes per launch of the 512x400x320 sweeps from the committed ncu summary,
+    when it was taken on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bound_512x400x320")
+
+
+def batch_short(P, args):
+    """A shortened batched workload: the 64 uneven FP32 solves, 200 steps each, one pool,
+    against the same instances one at a time in FP64 and FP32 (100 steps each, scaled),
+    with the mu error against the FP64 solves on four instances."""
+    import torch
+    from paper_1605_03958_gb300 import workloads
+    inst = workloads.batch_instances()
+    K = 200
+    need = sum(P.Pool.slot_bytes(**k) for k in inst)
+    pool = P.Pool(int(need * 1.05) + (64 << 20), max_slots=len(inst))
+    ids = [pool.add(**k) for k in inst]
+    pool.tune(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pool.step(K)
+    batch_s = time.perf_counter() - t0
+    obs = [pool.observables(i) for i in ids[:4]]
+    pool.close()
+    single = {}
+    for prec in ("f64", "f32"):
+        tot = 0.0
+        for k in inst:
+            so = P.Solver(k["nx"], k["ny"], k["nz"], k["dx"], dt=k["dt"], gamma=k["gamma"],
+                          nu=k["nu"], lam=k["lam"], g=k["g"], prec=prec)
+            so.init_gaussian()
+            so.step_imag(2)
+            so.sync()
+            t0 = time.perf_counter()
+            so.step_imag(100)
+            so.sync()
+            tot += (time.perf_counter() - t0) * K / 100
+            so.close()
+        single[prec] = len(inst) / tot
+    err = []
+    for k, o in zip(inst[:4], obs):
+        so = P.Solver(k["nx"], k["ny"], k["nz"], k["dx"], dt=k["dt"], gamma=k["gamma"],
+                      nu=k["nu"], lam=k["lam"], g=k["g"], prec="f64")
+        so.init_gaussian()
+        so.step_imag(K)
+        ref = so.observables()
+        so.close()
+        err.append(abs(o["mu"] - ref["mu"]) / abs(ref["mu"]))
+    v = len(inst) / batch_s
+    return {"workload": "64 uneven imag3d solves (extents {32..160}, trap U[0.5,3], g log-U[1,5000], "
+                        "h=0.2, dt=0.1h^2, seed 1605), 200 steps each",
+            "value": round(v, 3), "unit": "solves/s",
+            "one_at_a_time_f64": round(single["f64"], 3), "one_at_a_time_f32": round(single["f32"], 3),
+            "speedup_vs_f64": round(v / single["f64"], 2),
+            "mu_rel_vs_f64_max": max(err), "accuracy_instances": len(err)}
+
+
+def serve_short(P, args):
+    """A shortened serving run: the first 300 requests of the seeded stream (Poisson at
+    200 / s) through the continuous-batching server, and the leading 50 one at a time
+    with FP64 single solvers (arrivals on the wall clock in both)."""
+    import numpy as np
+    from paper_1605_03958_gb300 import workloads
+    from paper_1605_03958_gb300.serve import Server, serve_one_at_a_time
+
+    def summary(done):
+        lat = sorted(d["latency"] for d in done)
+        span = max(d["finished"] for d in done) - min(d["arrival"] for d in done)
+        return {"solves": len(done), "solves_per_s": round(len(done) / span, 3),
+                "p50_s": round(float(np.percentile(lat, 50)), 4),
+                "p99_s": round(float(np.percentile(lat, 99)), 4)}
+
+    reqs = workloads.serve_requests(300)
+    srv = Server(quantum=100)
+    done = srv.run(reqs, realtime=True)
+    srv.close()
+    head = reqs[:50]
+    f64 = serve_one_at_a_time(head, prec="f64", realtime=True)
+    by = {d["id"]: d for d in f64}
+    gerr = qerr = 0.0
+    for d in done:
+        if d["id"] not in by:
+            continue
+        w = by[d["id"]]["obs"]
+        if d["kind"] == "ground":
+            gerr = max(gerr, abs(d["obs"]["mu"] - w["mu"]) / abs(w["mu"]))
+        else:
+            qerr = max(qerr, abs(d["obs"]["energy"] - w["energy"]) / abs(w["energy"]))
+    return {"workload": "first 300 requests, Poisson arrivals at 200/s (seed 3958): 70 % ground "
+                        "state (2000 imaginary steps), 30 % quench (500..5000 real steps)",
+            "batched": summary(done),
+            "one_at_a_time_f64_first_50": summary(f64),
+            "accuracy_vs_f64_first_50": {"ground_mu_rel_max": gerr, "quench_energy_rel_max": qerr}}
+
+
 # ------------------------------------------------------------ CUDA arm
 
 def run_cuda(args):
@@ -280,17 +553,7 @@ def run_cuda(args):
     hbm, peak_kind = peaks()
     names = ["sweep_x", "sweep_y", "sweep_z"]
     info = s.info()
-    rt = "float" if args.prec == "f32" else "double"
-    L = info["trunc"]
-    c = "true" if real else "false"     # complex field
-    nm = "false" if real else "true"    # the z sweep sums the norm in imaginary time only
-    kernels = {
-        "sweep_x": (f"k_sweep_x_band<float,{c},{info['band_w']}>" if info["band_mask"] & 1 else
-                    f"k_sweep_x_stream<float,{c},{L}>" if info["fast_mask"] & 1 else f"k_sweep_x<{rt},{c}>"),
-        "sweep_y": (f"k_sweep_band_line<float,{c},1,false,{info['band_w']}>" if info["band_mask"] & 2 else
-                    f"k_sweep_stream<float,{c},1,false,{L}>" if info["fast_mask"] & 2 else f"k_sweep_y<{rt},{c}>"),
-        "sweep_z": (f"k_sweep_band_line<float,{c},2,{nm},{info['band_w']}>" if info["band_mask"] & 4 else
-                    f"k_sweep_stream<float,{c},2,{nm},{L}>" if info["fast_mask"] & 4 else f"k_sweep_z<{rt},{c},{nm}>")}
+    kernels = sweep_kernel_names(info, args.prec, real)
     per = {}
     for i, n in enumerate(names):
         if kn[i] == 0:   # a 2D solve has no z sweep
@@ -357,35 +620,17 @@ def run_cuda(args):
     torch.cuda.synchronize()
     warm_ms = a.elapsed_time(b) / K
 
-    # the other storage precision, same protocol on fewer steps
-    other = None
-    if args.f64_steps > 0:
-        oprec = "f64" if args.prec == "f32" else "f32"
-        so, ostep = make_solver(oprec)
-        for _ in range(3):
-            ostep(1)
-            flush()
-        torch.cuda.synchronize()
-        P.gp_set_timing(so.handle, True)
-        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.f64_steps)]
-        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.f64_steps)]
-        for k in range(args.f64_steps):
-            e0[k].record()
-            ostep(1)
-            e1[k].record()
-            flush()
-        torch.cuda.synchronize()
-        oms, okn = P.gp_get_timing(so.handle)
-        so.sync()
-        ototal = sum(e0[k].elapsed_time(e1[k]) for k in range(args.f64_steps))
-        ob = (8 if oprec == "f64" else 4) * (2 if real else 1)
-        other = {"prec": oprec, "value": round(NPTS * args.f64_steps / (ototal / 1e3), 1),
-                 "ms_per_step": round(ototal / args.f64_steps, 5), "steps": args.f64_steps,
-                 "sweeps_avg_ms": [round(oms[i] / max(okn[i], 1), 5) for i in range(3)],
-                 "hbm_frac_per_sweep": [round(2 * NPTS * ob / (oms[i] / max(okn[i], 1) / 1e3) / 1e9 / hbm, 3)
-                                        for i in range(3)]}
-        so.close()
-
+    # context (after the timed regions): the paper's precision (FP64 imaginary time on
+    # this grid, complex128 real time on the quench workload) with its per-sweep FP64
+    # ALU roofline; the same solve on a DRAM-bound grid; shortened batched and served
+    # workloads
+    paper = dram = batched = served = None
+    if args.context and world == 1:
+        csum = clk.summary()
+        paper = paper_precision(P, args, flush, hbm, (csum or {}).get("sm_mhz") or 2070.0)
+        dram = dram_bound(P, args, flush, hbm)
+        batched = batch_short(P, args)
+        served = serve_short(P, args)
     obs = s.observables()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -408,7 +653,8 @@ def run_cuda(args):
         "cpu_baseline": cpu,
         "context": {"warm_l2_ms_per_step": round(warm_ms, 5),
                     "warm_l2_value": round(NPTS / (warm_ms / 1e3), 1),
-                    "other_precision": other,
+                    "paper_precision": paper, "dram_bound": dram,
+                    "batched": batched, "served": served,
                     "mu_after_run": obs["mu"], "norm_after_run": obs["norm"]},
     }
     s.close()
