@@ -212,7 +212,8 @@ def sweep_kernel_names(info, prec, real):
         return {"sweep_x": f"k_sweep_x64<{c}>", "sweep_y": f"k_sweep_line64<{c},1,false>",
                 "sweep_z": f"k_sweep_line64<{c},2,{nm}>"}
     return {
-        "sweep_x": (f"k_sweep_x_band<float,{c},{W}>" if info["band_mask"] & 1 else
+        "sweep_x": (f"k_sweep_x_reg<{c},{W}>" if info.get("x_reg") else
+                    f"k_sweep_x_band<float,{c},{W}>" if info["band_mask"] & 1 else
                     f"k_sweep_x_stream<float,{c},{L}>" if info["fast_mask"] & 1 else f"k_sweep_x<{rt},{c}>"),
         "sweep_y": (f"k_sweep_band_line<float,{c},1,false,{W}>" if info["band_mask"] & 2 else
                     f"k_sweep_stream<float,{c},1,false,{L}>" if info["fast_mask"] & 2 else f"k_sweep_y<{rt},{c}>"),

@@ -38,7 +38,9 @@
  *     stream).  gp_step_* return as soon as the work is queued; gp_sync,
  *     gp_observables, gp_get_psi and the density calls wait for it, and report
  *     GP_ERR_NONFINITE when a step produced a non-finite or zero norm and
- *     GP_ERR_TIMEOUT when a kernel's bounded wait on its own copies ran out.
+ *     GP_ERR_TIMEOUT when a kernel's bounded wait on its own copies ran out (and,
+ *     in a library built with -DGP_CHECK, GP_ERR_BOUNDS when a kernel's bounds
+ *     check found an index outside its buffer: the access is skipped, nothing traps).
  *   - Host-side arrays use the layout psi[k][j][i] (x fastest, index
  *     (k*ny + j)*nx + i), FP64, complex values interleaved (re, im), whatever the
  *     storage precision on the device.
@@ -60,6 +62,7 @@ extern "C" {
 #define GP_ERR_NONFINITE (-4) /* the norm became non-finite or zero            */
 #define GP_ERR_TIMEOUT (-5)   /* a kernel's bounded wait gave up               */
 #define GP_ERR_STATE (-6)     /* call not valid in the solver's current mode   */
+#define GP_ERR_BOUNDS (-7)    /* a bounds check of a GP_CHECK build failed     */
 
 /* Storage precision of the field.  FP64: double / complex double, all arithmetic
  * in FP64.  FP32: float / complex float storage and sweeps; elimination
@@ -238,7 +241,8 @@ int gp_get_timing(gp_solver* s, double ms[3], long long launches[3]);
  *           shared-memory line tiles (decaying coupling cut below FP32 rounding, see
  *           gp_sweeps.cu), bit 3 + a when that kernel is the banded operator, bits
  *           8..11 the largest band half-width W, bits 12 + a when sweep a uses the
- *           FP64 line-streaming kernels (FP64 field; gp_sweeps64.cu),
+ *           FP64 line-streaming kernels (FP64 field; gp_sweeps64.cu), bit 15 when the
+ *           banded x sweep holds each row in registers (k_sweep_x_reg),
  *   info[7] the truncation depth L of the streaming recurrences (0 when none).
  * GP_SWEEP_KERNELS=tile in the environment at gp_create time makes every sweep
  * use the tile kernels; =stream keeps the FP32 sweeps on the streaming recurrences

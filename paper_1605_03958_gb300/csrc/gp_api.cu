@@ -10,6 +10,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -242,6 +243,12 @@ void cn_coefficients(int n, std::complex<double> a, std::vector<std::complex<dou
 bool force_tile() {
   const char* v = std::getenv("GP_SWEEP_KERNELS");
   return v && std::strcmp(v, "tile") == 0;
+}
+// GP_X_REG=0 keeps the banded x sweep on the copy-fed kernel for rows that the
+// register-row kernel could take (A/B measurements).
+bool x_reg_enabled() {
+  const char* v = std::getenv("GP_X_REG");
+  return !(v && std::strcmp(v, "0") == 0);
 }
 // GP_BAND_PREFETCH=0 keeps the banded y / z sweeps' turn loads in registers instead
 // of copying them to shared memory one turn ahead (A/B measurements).
@@ -502,6 +509,19 @@ void fill_sweep_params(gp_solver* s) {
           s->band_w[m][0] = 0;
           q.band_w = 0;
         }
+        // real rows of nx = 8 m <= 256 points: the row in registers, no copies (complex
+        // rows measured no faster that way)
+        int rbps = 0;
+        if (q.band_w && m == 0 && gpk::x_reg_fits(p.nx, q.band_w) && x_reg_enabled() &&
+            gpk::x_reg_prepare(q.band_w, m == 1, &rbps) == cudaSuccess && rbps > 0) {
+          const long long rows = (long long)p.ny * p.nz;
+          const long long cap = (long long)s->nsm * rbps * gpk::kXRegWarps;
+          q.band_rows = (int)((rows + cap - 1) / cap);
+          const long long warps = (rows + q.band_rows - 1) / q.band_rows;
+          s->fast_grid[m][0] = (int)((warps + gpk::kXRegWarps - 1) / gpk::kXRegWarps);
+          q.band_reg = 1;
+        }
+        cudaGetLastError();
       }
       if (a > 0 && s->band_w[m][a]) {
         std::memcpy(q.band_wt, s->band_wt[m][a], sizeof q.band_wt);
@@ -807,7 +827,16 @@ cudaEvent_t take_event(gp_solver* s) {
   return ev;
 }
 
+// NVTX range around a host-side call (shows each sweep launch and step call on a
+// profiler's timeline; a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <class R> int run_sweep(gp_solver* s, int axis) {
+  static const char* const kNames[3] = {"gp sweep x", "gp sweep y", "gp sweep z"};
+  NvtxRange range(kNames[axis]);
   const int m = s->is_complex ? 1 : 0;
   SweepParams q = s->sp[m][axis];
   if (axis == 0 && s->kinetic_only) q.pw = 0;
@@ -819,7 +848,9 @@ template <class R> int run_sweep(gp_solver* s, int axis) {
     GP_CUDA(s, cudaEventRecord(tl.start, s->stream));
   }
   cudaError_t e;
-  if (axis == 0 && q.band_w)
+  if (axis == 0 && q.band_w && q.band_reg)
+    e = gpk::launch_sweep_x_reg(q, m == 1, s->fast_grid[m][0], s->stream);
+  else if (axis == 0 && q.band_w)
     e = gpk::launch_sweep_x_band(q, m == 1, s->fast_grid[m][0], s->stream);
   else if (q.band_w)
     e = gpk::launch_sweep_band_line(axis, q, m == 1, s->fast_grid[m][axis], s->stream);
@@ -1017,6 +1048,8 @@ int check_status(gp_solver* s) {
   GP_CUDA(s, cudaStreamSynchronize(s->stream));
   if (st == 0) return GP_OK;
   GP_CUDA(s, cudaMemsetAsync(s->status, 0, sizeof(int), s->stream));
+  if (st & gpk::kStatusBounds)
+    return fail(s, GP_ERR_BOUNDS, "a kernel's bounds check found an index outside its buffer");
   if (st & gpk::kStatusTimeout)
     return fail(s, GP_ERR_TIMEOUT, "a kernel's bounded wait on its tile copy ran out");
   return fail(s, GP_ERR_NONFINITE, "the norm became non-finite or zero");
@@ -1253,6 +1286,7 @@ int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex) {
 int gp_step_imag(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
   if (s->is_complex) return fail(s, GP_ERR_STATE, "imaginary-time steps need a real field");
+  NvtxRange range("gp_step_imag");
   return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
 }
 
@@ -1262,6 +1296,7 @@ int gp_step_real(gp_solver* s, long nsteps) {
     const int rc = promote_to_complex(s);
     if (rc != GP_OK) return rc;
   }
+  NvtxRange range("gp_step_real");
   return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
 }
 
@@ -1413,6 +1448,7 @@ int gp_get_info(const gp_solver* s, long long info[8]) {
   }
   info[6] |= (long long)wmax << 8;
   if (s->line64) info[6] |= 7LL << 12;
+  if (s->sp[m][0].band_reg) info[6] |= 1LL << 15;
   info[7] = std::max(s->trunc[m][0], std::max(s->trunc[m][1], s->trunc[m][2]));
   return GP_OK;
 }
@@ -1430,6 +1466,7 @@ const char* gp_strerror(int code) {
     case GP_ERR_NONFINITE: return "non-finite or zero norm";
     case GP_ERR_TIMEOUT: return "kernel wait timed out";
     case GP_ERR_STATE: return "invalid in the current mode";
+    case GP_ERR_BOUNDS: return "bounds check failed (GP_CHECK build)";
     default: return "unknown error";
   }
 }

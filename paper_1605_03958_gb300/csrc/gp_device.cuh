@@ -12,6 +12,23 @@
 
 namespace gpk {
 
+// ------------------------------------------------------------------ bounds checks
+
+// Built with -DGP_CHECK, GP_IN(i, n, status) is true when 0 <= i < n and otherwise
+// records kStatusBounds in the solver's status word and is false, so that the access
+// it guards is skipped (nothing traps; the host reports GP_ERR_BOUNDS).  In a normal
+// build it is the constant true and the guarded code is unchanged.
+#ifdef GP_CHECK
+__device__ __forceinline__ bool check_index(long long i, long long n, int* status) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(status, kStatusBounds);
+  return false;
+}
+#define GP_IN(i, n, status) ::gpk::check_index((long long)(i), (long long)(n), (status))
+#else
+#define GP_IN(i, n, status) true
+#endif
+
 // ------------------------------------------------------------------ PTX wrappers
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -217,6 +234,99 @@ __device__ __forceinline__ void norm_finish(double acc, double* partials, unsign
     *scale_out = rsqrt(norm);
     *counter = 0u;
   }
+}
+
+// Compensated FP32 pair (float-float): the value is hi + lo with |lo| <= ulp(hi) / 2.
+// ff_add takes the error-free two-sum of the high parts (Knuth), adds the low parts to
+// its error and renormalises: about 2^-44 relative error per addition, all on the
+// FP32 pipe.  The FP32 sweeps sum their renormalisation norm this way: FP64 is narrow
+// on this part, and a dependent FP64 tree at the end of every block held the z sweep
+// back by about 4 us at 240 x 200 x 160.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bv = s - a.hi;
+  const float e = ((a.hi - (s - bv)) + (b.hi - bv)) + (a.lo + b.lo);
+  const float hi = s + e;
+  return FF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ FF ff_shfl_down(FF v, int o) {
+  return FF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p) {
+  unsigned int old;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
+// norm_finish with the block's sums in float-float: every thread's FF value is summed
+// in a fixed order (warp shuffle tree, warps in order) into partials[bid] (one FF per
+// block, stored as a float pair); the last block to finish sums the nb partials in a
+// fixed order over its threads, then in FP64 forms norm = (hi + lo) dV and writes the
+// factor 1 / sqrt(norm).  With G > 1 the blocks take their tickets on G group counters
+// (block b on gcounter[b mod G]) and only the last block of each group on `counter`:
+// hundreds of blocks finishing together otherwise queue on one address at the L2.
+// The acquire-release tickets chain, so the last block sees every partial.  The last
+// block resets every counter it used.
+__device__ __forceinline__ void norm_finish_ff(FF acc, FF* partials, unsigned int* counter,
+                                               unsigned int nb, unsigned int bid, double* scale_out,
+                                               int* status, double dV,
+                                               unsigned int* gcounter = nullptr, int G = 1) {
+  __shared__ FF wpart_ff[32];
+  __shared__ int last_ff;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) acc = ff_add(acc, ff_shfl_down(acc, o));
+  if (lane == 0) wpart_ff[warp] = acc;
+  __syncthreads();
+  const unsigned int ngroups = G > 1 ? min((unsigned int)G, nb) : 1u;
+  if (threadIdx.x == 0) {
+    FF b = wpart_ff[0];
+    for (int w = 1; w < nw; ++w) b = ff_add(b, wpart_ff[w]);
+    partials[bid] = b;
+    // release of this block's partial and, for the last block, acquire of all the
+    // others' (see norm_finish)
+    bool last = false;
+    if (G > 1) {
+      const unsigned int g = bid % (unsigned int)G;
+      const unsigned int gsize = (nb - g + G - 1) / G;   // blocks b < nb with b mod G == g
+      if (atom_add_acq_rel(gcounter + g) == gsize - 1) last = atom_add_acq_rel(counter) == ngroups - 1;
+    } else {
+      last = atom_add_acq_rel(counter) == nb - 1;
+    }
+    last_ff = last;
+  }
+  __syncthreads();
+  if (!last_ff) return;
+  // a thread's partials t, t + T, ... are loaded eight at a time, all in flight
+  // together (one L2 round trip per eight, not per partial), then added in order
+  FF s = FF{0.f, 0.f};
+  const unsigned int T = blockDim.x;
+  for (unsigned int t0 = threadIdx.x; t0 < nb; t0 += 8 * T) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const unsigned int t = t0 + q * T;
+      v[q] = t < nb ? __ldcg(reinterpret_cast<const float2*>(partials) + t) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = ff_add(s, FF{v[q].x, v[q].y});
+  }
+  for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_down(s, o));
+  if (lane == 0) wpart_ff[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    FF b = wpart_ff[0];
+    for (int w = 1; w < nw; ++w) b = ff_add(b, wpart_ff[w]);
+    const double norm = ((double)b.hi + (double)b.lo) * dV;
+    if (!(norm > 0.0) || !isfinite(norm)) atomicOr(status, kStatusNonFinite);
+    *scale_out = rsqrt(norm);
+    *counter = 0u;
+  }
+  if (G > 1)
+    for (unsigned int g = threadIdx.x; g < ngroups; g += blockDim.x) gcounter[g] = 0u;
 }
 
 // ------------------------------------------------------------------- arithmetic

@@ -15,6 +15,7 @@ namespace gpk {
 // Status bits written by kernels into the solver's device status word.
 constexpr int kStatusNonFinite = 1;  // norm non-finite or zero (imaginary time)
 constexpr int kStatusTimeout = 2;    // a bounded wait on a tile copy ran out
+constexpr int kStatusBounds = 4;     // GP_CHECK builds: an index fell outside its buffer
 
 // Bounded waits on a block's own copies give up after this much wall time.  A
 // solver's first wait on each copy takes its own limit (SweepParams::wait_ns, this
@@ -31,10 +32,18 @@ constexpr int kMaxBox = 256;
 // Warps per block of the banded FP32 x sweep (each warp works on its own rows): few
 // large blocks fill the SMs sooner than many small ones when the sweep starts.
 constexpr int kBandWarps = 12;
+// Warps per block of the register-row banded x sweep (each warp on its own rows).
+constexpr int kXRegWarps = 8;
 // Warps per block of the batched x sweep (one work item per warp).
 constexpr int kBatchXWarps = 4;
 // Largest half-width of the banded operators (weights arrays hold 2 kBandHalfMax + 1).
 constexpr int kBandHalfMax = 8;
+
+// Ticket counters of the fused norm: a solver's counters[0] is the top counter,
+// counters[kNormGroupBase .. + kNormGroups) the group counters (the solver's scalar
+// area holds 48 counters).
+constexpr int kNormGroups = 32;
+constexpr int kNormGroupBase = 16;
 
 // Fixed launch shape of the reductions, so that their summation order (and hence
 // their result) does not depend on the device.
@@ -75,6 +84,7 @@ struct SweepParams {
   int band_group;        // x: rows per group (worked on together by the warp's lanes)
   int band_seg;          // y / z: points per line segment (a multiple of 2 band_w + 1)
   int band_cp;           // y / z: 1 = next turn's inputs copied to shared memory ahead (cp.async)
+  int band_reg;          // x: 1 = the row in registers (k_sweep_x_reg)
   float band_dtg;        // x: dt g in FP32
   // pointwise substep (x sweep only)
   int pw;                // 1: pointwise substep fused on load; 0: kinetic-only step
@@ -169,6 +179,11 @@ cudaError_t x_band_prepare(int w, bool complex_field, bool grouped, size_t smem,
                            int* blocks_per_sm);
 cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int grid,
                                 cudaStream_t st);
+// FP32 banded x sweep with the row in registers (rows of nx = 8 m <= 256, W in {3, 5}):
+// blocks of kXRegWarps warps, no shared memory; band_rows rows per warp.
+bool x_reg_fits(int nx, int w);
+cudaError_t x_reg_prepare(int w, bool complex_field, int* blocks_per_sm);
+cudaError_t launch_sweep_x_reg(const SweepParams& p, bool complex_field, int grid, cudaStream_t st);
 // FP32 banded y / z sweeps (out of place like the streaming ones), blocks of 128 threads.
 cudaError_t launch_sweep_band_line(int axis, const SweepParams& p, bool complex_field, int grid,
                                    cudaStream_t st);

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)W * P * sizeof(E));
   E* gtile = reinterpret_cast<E*>(p.psi) + r0 * P;
   const uint32_t bytes = (uint32_t)((size_t)rows * P * sizeof(E));
+  if (!GP_IN((r0 + rows) * P - 1, nrows * P, p.status)) return;
 
   if (lane == 0) {
     mbar_init(bar, 1);
@@ -682,6 +683,14 @@ __device__ __forceinline__ float shfl_e(float v, int src) { return __shfl_sync(0
 __device__ __forceinline__ float2 shfl_e(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
+__device__ __forceinline__ float shfl_up_e(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ float2 shfl_up_e(float2 v, int d) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float shfl_down_e(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ float2 shfl_down_e(float2 v, int d) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
 
 // What one warp of the banded x sweep works on: nrow consecutive rows from row0 of
 // one field, taken G rows at a time (a group), streamed through S shared-memory
@@ -1032,8 +1041,132 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.slot_elems = slot_elems;
   a.pw = p.pw;
   a.dtg = p.band_dtg;
+  if (!GP_IN(row0 + nrow - 1, nrows, p.status)) return;
   if (GROUPED) x_band_rows<R, CPLX, W>(a, full, slots);
   else x_band_rows_single<R, CPLX, W>(a, full, slots);
+}
+
+// Banded x sweep with the row in registers, for rows of nx = 8 m <= 256 points and
+// W <= 7: lane l owns the eight elements [8l, 8l + 8) of the warp's current row (two
+// 16-byte vectors of a real field, four of a complex one), loaded coalesced with the
+// next row's already in flight.  The pending factor and the pointwise substep are
+// applied in registers; the W neighbours on each side come from lanes l - 1 and l + 1
+// by shuffles, and at the row's ends the odd images (-v mirrored about the ghosts -1
+// and nx, zero at the ghosts) come from the lane's own elements (8 >= W + 1).  No
+// shared memory, copies or waits: the instructions per point are the arithmetic plus
+// a few shuffles, which is what bounds the copy-fed kernel above.  Each warp works on
+// a_rows consecutive rows; every warp of the launch is resident at once.
+template <bool CPLX, int W>
+__global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_constant__ SweepParams p) {
+  using F = Field<float, CPLX>;
+  using E = typename F::E;
+  constexpr int EPT = 16 / (int)sizeof(E);   // elements per 16-byte vector
+  constexpr int VPL = 8 / EPT;               // vectors per lane
+  static_assert(W <= 7, "images from the lane's own eight elements");
+  const int lane = threadIdx.x & 31;
+  const long long nrows = (long long)p.ny * p.nz;
+  const long long row0 = ((long long)blockIdx.x * kXRegWarps + (threadIdx.x >> 5)) * p.band_rows;
+  const int nrow = (int)max(0LL, min((long long)p.band_rows, nrows - row0));
+  const int nx = p.nx, pitch = p.pitch;
+  const int x0 = 8 * lane;
+  const bool act = x0 < nx;                  // lanes past the row hold zeros
+  const bool first = lane == 0, last = x0 + 8 == nx;
+  E wt[W + 1];   // wt[0] = w_0 - 1, wt[k] = w_k
+#pragma unroll
+  for (int k = 0; k <= W; ++k) wt[k] = reinterpret_cast<const E*>(p.band_wt)[W + k];
+  E fx[8];
+  {
+    const float4* fxv = reinterpret_cast<const float4*>(static_cast<const E*>(p.band_fx) + x0);
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+      const float4 f = act ? __ldg(fxv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) fx[q * EPT + e] = reinterpret_cast<const E*>(&f)[e];
+    }
+  }
+  pdl_begin();
+  if (nrow == 0) return;
+  const float s = (float)(*p.scale);
+  const float dtg = p.band_dtg;
+  const bool pw = p.pw != 0;
+  E* field = static_cast<E*>(p.psi);
+  const E* fyz = static_cast<const E*>(p.band_fyz);
+  const long long nel = nrows * pitch;   // field elements (bounds checks)
+  auto load_row = [&](long long r, float4 (&buf)[VPL]) {
+    const float4* src = reinterpret_cast<const float4*>(field + (size_t)r * pitch + x0);
+#pragma unroll
+    for (int q = 0; q < VPL; ++q)
+      buf[q] = act && GP_IN(r * pitch + x0 + (q + 1) * EPT - 1, nel, p.status)
+                   ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  // row r's pointwise substep, banded operator and store, from its loaded vectors
+  auto process = [&](long long r, const float4 (&cur)[VPL], E fr) {
+    E v[8];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q)
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[q * EPT + e] = reinterpret_cast<const E*>(&cur[q])[e];
+    // pending factor and pointwise substep (the warp takes the polynomial branch when
+    // every argument allows it)
+    float y[8];
+    float ymax = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[e] = F::scaled(v[e], s);
+      y[e] = dtg * F::abs2(v[e]);
+      ymax = fmaxf(ymax, fabsf(y[e]));
+    }
+    if (!pw) {
+    } else if (__all_sync(0xffffffffu, ymax <= 0.0625f)) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = F::nonlinear_small(v[e], F::mul(fx[e], fr), y[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = F::nonlinear_full(v[e], F::mul(fx[e], fr), y[e]);
+    }
+    // halo: lo[m] = position x0 - m, hi[m] = position x0 + 7 + m (m = 1..W)
+    E lo[W + 1], hi[W + 1];
+#pragma unroll
+    for (int m = 1; m <= W; ++m) {
+      lo[m] = shfl_up_e(v[8 - m], 1);
+      hi[m] = shfl_down_e(v[m - 1], 1);
+      // odd images: position -m is 0 (m = 1) or -v[m - 2]; position nx - 1 + m is 0
+      // (m = 1) or -v[9 - m]
+      if (first) lo[m] = m == 1 ? F::zero() : F::scaled(v[m - 2], -1.f);
+      if (last) hi[m] = m == 1 ? F::zero() : F::scaled(v[9 - m], -1.f);
+    }
+    auto win = [&](int j) -> E { return j < 0 ? lo[-j] : (j >= 8 ? hi[j - 7] : v[j]); };
+    E o[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      E acc = F::mul(wt[0], v[e]);
+#pragma unroll
+      for (int k = 1; k <= W; ++k) acc = F::chain(wt[k], F::add(win(e - k), win(e + k)), acc);
+      o[e] = F::add(v[e], acc);
+    }
+    if (act && GP_IN(r * pitch + x0 + 7, nel, p.status)) {
+      float4* dst = reinterpret_cast<float4*>(field + (size_t)r * pitch + x0);
+#pragma unroll
+      for (int q = 0; q < VPL; ++q) dst[q] = *reinterpret_cast<const float4*>(&o[q * EPT]);
+    }
+  };
+  // the next row's loads are in flight while a row is processed (deeper prefetch,
+  // in registers or through shared memory, measured slower at 240 x 200 x 160)
+  float4 cur[VPL], nxt[VPL];
+  load_row(row0, cur);
+  E fr = fyz[row0];
+  for (int i = 0; i < nrow; ++i) {
+    const long long r = row0 + i;
+    E frn = fr;
+    if (i + 1 < nrow) {
+      load_row(r + 1, nxt);
+      frn = fyz[r + 1];
+    }
+    process(r, cur, fr);
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) cur[q] = nxt[q];
+    fr = frn;
+  }
 }
 
 // Batched x sweep: warp w of the launch takes work item w (rows of one slot).
@@ -1090,11 +1223,13 @@ template <class E> struct LineArgs {
   E* out;                // output field, same layout
   const E* wt;           // w_{k-W}, k = 0 .. 2W (centre as w_0 - 1)
   int nx, ny, nz, n, pitch, Ls;
+  int* status;           // bounds checks of GP_CHECK builds
 };
 
-// Thread t's segment of one line; returns the FP64 sum of |u|^2 it stored (NORM).
+// Thread t's segment of one line; returns the sum of |u|^2 it stored (NORM): FP32 within
+// a turn, float-float across turns.
 template <class R, bool CPLX, int AXIS, bool NORM, int W>
-__device__ __forceinline__ double band_line_thread(const LineArgs<typename Field<R, CPLX>::E>& p,
+__device__ __forceinline__ FF band_line_thread(const LineArgs<typename Field<R, CPLX>::E>& p,
                                                    long long t) {
   using F = Field<R, CPLX>;
   using E = typename F::E;
@@ -1105,7 +1240,7 @@ __device__ __forceinline__ double band_line_thread(const LineArgs<typename Field
   const int nother = AXIS == 1 ? p.nz : p.ny;
   const int nseg = (n + Ls - 1) / Ls;
   const E* wt = p.wt;
-  double acc = 0.0;
+  FF acc = FF{0.f, 0.f};
   if (t < (long long)nvec * nother * nseg) {
     const int xv = (int)(t % nvec);
     const long long rest = t / nvec;
@@ -1119,10 +1254,16 @@ __device__ __forceinline__ double band_line_thread(const LineArgs<typename Field
     const int j0 = sg * Ls, j1 = min(n, j0 + Ls);
     const bool interior = j0 >= W && j0 + Ls + W <= n;
     // input j of the odd extension about the ghosts -1 and n
+    // 16-byte vectors of the field, and this line's first one (bounds checks)
+    const long long nvec_all = (long long)p.nz * p.ny * (long long)pitch / EPT, v0 = (long long)(base / EPT);
     auto ld = [&](int j) -> float4 {
-      if (interior || (j >= 0 && j < n)) return in[(size_t)j * sv];
+      if (interior || (j >= 0 && j < n))
+        return GP_IN(v0 + (long long)j * sv, nvec_all, p.status) ? in[(size_t)j * sv]
+                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
       if (j == -1 || j == n) return make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 v = in[(size_t)(j < 0 ? -2 - j : 2 * n - j) * sv];
+      const int m = j < 0 ? -2 - j : 2 * n - j;
+      const float4 v = GP_IN(v0 + (long long)m * sv, nvec_all, p.status) ? in[(size_t)m * sv]
+                                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
       return make_float4(-v.x, -v.y, -v.z, -v.w);
     };
     float4 ring[P];
@@ -1154,7 +1295,8 @@ __device__ __forceinline__ double band_line_thread(const LineArgs<typename Field
             }
             oe[e] = F::add(c[e], a);
           }
-          if (valid == EPT) {
+          if (!GP_IN(v0 + (long long)j * sv, nvec_all, p.status)) {
+          } else if (valid == EPT) {
             out[(size_t)j * sv] = ov;
             if (NORM) {
 #pragma unroll
@@ -1169,7 +1311,7 @@ __device__ __forceinline__ double band_line_thread(const LineArgs<typename Field
           }
         }
       }
-      if (NORM) acc += (double)part;
+      if (NORM) acc = ff_add(acc, FF{part, 0.f});
     }
   }
   return acc;
@@ -1183,7 +1325,7 @@ __device__ __forceinline__ double band_line_thread(const LineArgs<typename Field
 // array of 16-byte slots; a thread uses only its own.  The odd images past the
 // line's ends are copied from their mirror positions and negated when read.
 template <class R, bool CPLX, int AXIS, bool NORM, int W>
-__device__ __forceinline__ double band_line_thread_cp(const LineArgs<typename Field<R, CPLX>::E>& p,
+__device__ __forceinline__ FF band_line_thread_cp(const LineArgs<typename Field<R, CPLX>::E>& p,
                                                       long long t, float4* slots) {
   using F = Field<R, CPLX>;
   using E = typename F::E;
@@ -1195,7 +1337,7 @@ __device__ __forceinline__ double band_line_thread_cp(const LineArgs<typename Fi
   const int nseg = (n + Ls - 1) / Ls;
   const E* wt = p.wt;
   const int bt = blockDim.x, tid = threadIdx.x;
-  double acc = 0.0;
+  FF acc = FF{0.f, 0.f};
   if (t < (long long)nvec * nother * nseg) {
     const int xv = (int)(t % nvec);
     const long long rest = t / nvec;
@@ -1209,10 +1351,16 @@ __device__ __forceinline__ double band_line_thread_cp(const LineArgs<typename Fi
     const int j0 = sg * Ls, j1 = min(n, j0 + Ls);
     const bool interior = j0 >= W && j0 + Ls + W <= n;
     // input j of the odd extension about the ghosts -1 and n
+    // 16-byte vectors of the field, and this line's first one (bounds checks)
+    const long long nvec_all = (long long)p.nz * p.ny * (long long)pitch / EPT, v0 = (long long)(base / EPT);
     auto ld = [&](int j) -> float4 {
-      if (interior || (j >= 0 && j < n)) return in[(size_t)j * sv];
+      if (interior || (j >= 0 && j < n))
+        return GP_IN(v0 + (long long)j * sv, nvec_all, p.status) ? in[(size_t)j * sv]
+                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
       if (j == -1 || j == n) return make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 v = in[(size_t)(j < 0 ? -2 - j : 2 * n - j) * sv];
+      const int m = j < 0 ? -2 - j : 2 * n - j;
+      const float4 v = GP_IN(v0 + (long long)m * sv, nvec_all, p.status) ? in[(size_t)m * sv]
+                                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
       return make_float4(-v.x, -v.y, -v.z, -v.w);
     };
     // copy of turn b's inputs j = b + u + W (u < P) into slot set h
@@ -1227,6 +1375,7 @@ __device__ __forceinline__ double band_line_thread_cp(const LineArgs<typename Fi
           src = j < 0 ? -2 - j : (j > n ? 2 * n - j : j);
           if (!ok) src = 0;
         }
+        if (!GP_IN(v0 + (long long)src * sv, nvec_all, p.status)) ok = false, src = 0;
         cp_async16_zfill(slots + (size_t)(h * P + u) * bt + tid, in + (size_t)src * sv, ok);
       }
     };
@@ -1265,7 +1414,8 @@ __device__ __forceinline__ double band_line_thread_cp(const LineArgs<typename Fi
             }
             oe[e] = F::add(c[e], a);
           }
-          if (valid == EPT) {
+          if (!GP_IN(v0 + (long long)j * sv, nvec_all, p.status)) {
+          } else if (valid == EPT) {
             out[(size_t)j * sv] = ov;
             if (NORM) {
 #pragma unroll
@@ -1280,7 +1430,7 @@ __device__ __forceinline__ double band_line_thread_cp(const LineArgs<typename Fi
           }
         }
       }
-      if (NORM) acc += (double)part;
+      if (NORM) acc = ff_add(acc, FF{part, 0.f});
     }
     cp_async_wait<0>();
   }
@@ -1301,15 +1451,18 @@ __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__
   a.n = p.n;
   a.pitch = p.pitch;
   a.Ls = p.band_seg;
+  a.status = p.status;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc;
+  FF acc;
   if constexpr (CP) {
     extern __shared__ __align__(16) float4 band_slots[];
     acc = band_line_thread_cp<R, CPLX, AXIS, NORM, W>(a, t, band_slots);
   } else {
     acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, t);
   }
-  if (NORM) norm_block_finish(acc, p);
+  if (NORM)
+    norm_finish_ff(acc, reinterpret_cast<FF*>(p.partials), p.counter, gridDim.x, blockIdx.x,
+                   p.scale_out, p.status, p.dV, p.counter + kNormGroupBase, kNormGroups);
 }
 
 // Batched y / z sweep: block b of the launch is block blk of nblk of one slot; the
@@ -1330,8 +1483,11 @@ __global__ void __launch_bounds__(128) k_batch_band_line(const __grid_constant__
   a.n = AXIS == 1 ? d.ny : d.nz;
   a.pitch = d.pitch;
   a.Ls = d.seg[AXIS];
-  const double acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, (long long)lb.blk * blockDim.x + threadIdx.x);
-  if (NORM) norm_finish(acc, d.partials, d.counter, (unsigned int)lb.nblk, (unsigned int)lb.blk, d.scale, b.status, d.dV);
+  a.status = b.status;
+  const FF acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, (long long)lb.blk * blockDim.x + threadIdx.x);
+  if (NORM)
+    norm_finish_ff(acc, reinterpret_cast<FF*>(d.partials), d.counter, (unsigned int)lb.nblk,
+                   (unsigned int)lb.blk, d.scale, b.status, d.dV);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1464,6 +1620,28 @@ cudaError_t x_band_prepare(int w, bool complex_field, bool grouped, size_t smem,
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * kBandWarps, smem);
+}
+
+static void (*x_reg_kernel_for(int w, bool cplx))(SweepParams) {
+  switch (w) {
+    case 3: return cplx ? k_sweep_x_reg<true, 3> : k_sweep_x_reg<false, 3>;
+    case 5: return cplx ? k_sweep_x_reg<true, 5> : k_sweep_x_reg<false, 5>;
+    default: return nullptr;
+  }
+}
+
+bool x_reg_fits(int nx, int w) { return nx % 8 == 0 && nx <= 256 && (w == 3 || w == 5); }
+
+cudaError_t x_reg_prepare(int w, bool complex_field, int* blocks_per_sm) {
+  void (*k)(SweepParams) = x_reg_kernel_for(w, complex_field);
+  if (!k) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * kXRegWarps, 0);
+}
+
+cudaError_t launch_sweep_x_reg(const SweepParams& p, bool complex_field, int grid, cudaStream_t st) {
+  void (*k)(SweepParams) = x_reg_kernel_for(p.band_w, complex_field);
+  if (!k) return cudaErrorInvalidValue;
+  return launch_pdl(k, grid, 32 * kXRegWarps, 0, st, p);
 }
 
 cudaError_t launch_sweep_x_band(const SweepParams& p, bool complex_field, int grid,

@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(kX64Warps * 32) k_sweep_x64(const __grid_const
 #pragma unroll
       for (int u = 0; u < NG; ++u) {
         const int rho = g0 + u * RPI + lr;
-        xv[u] = (cin && rho < rows) ? field[(size_t)rho * P + col] : F::zero();
+        xv[u] = (cin && rho < rows && GP_IN((r0 + rho) * P + col, nrows * P, p.status))
+                    ? field[(size_t)rho * P + col] : F::zero();
         rf[u] = rowf[rho];
       }
       if (!pw) {
@@ -241,7 +242,8 @@ __global__ void __launch_bounds__(kX64Warps * 32) k_sweep_x64(const __grid_const
 #pragma unroll 8
     for (int rr = 0; rr < 32; rr += RPI) {
       const int rho = rr + lr;
-      if (rho < rows) field[(size_t)rho * P + col] = b[rho * LD + lc];
+      if (rho < rows && GP_IN((r0 + rho) * P + col, nrows * P, p.status))
+        field[(size_t)rho * P + col] = b[rho * LD + lc];
     }
   };
   // forward values of chunk c's v (lane = row), in place; the element after the
@@ -295,7 +297,8 @@ __global__ void __launch_bounds__(kX64Warps * 32) k_sweep_x64(const __grid_const
 #pragma unroll 8
       for (int rr = 0; rr < 32; rr += RPI) {
         const int rho = rr + lr;
-        b[rho * LD + lc] = (col < nx && rho < rows) ? field[(size_t)rho * P + col] : F::zero();
+        b[rho * LD + lc] = (col < nx && rho < rows && GP_IN((r0 + rho) * P + col, nrows * P, p.status))
+                               ? field[(size_t)rho * P + col] : F::zero();
       }
       __syncwarp();
     }
@@ -319,12 +322,15 @@ __global__ void __launch_bounds__(kLineThreads) k_sweep_line64(const __grid_cons
   const long long nlines = (long long)nx * (AXIS == 1 ? p.nz : p.ny);
   const long long g = (long long)blockIdx.x * kLineThreads + threadIdx.x;
   double acc = 0.0;
-  if (g < nlines) {
-    const int i = (int)(g % nx);
-    const long long c = g / nx;
-    const size_t P = (size_t)p.pitch;
-    const size_t stride = AXIS == 1 ? P : P * (size_t)p.ny;
-    E* line = static_cast<E*>(p.psi) + (AXIS == 1 ? (size_t)c * P * p.ny : (size_t)c * P) + i;
+  const int i = (int)(g % nx);
+  const long long c = g / nx;
+  const size_t P = (size_t)p.pitch;
+  const size_t stride = AXIS == 1 ? P : P * (size_t)p.ny;
+  const size_t first = (AXIS == 1 ? (size_t)c * P * p.ny : (size_t)c * P) + i;
+  // the line's last element inside the field (bounds checks; the block still reaches
+  // the norm's barriers)
+  if (g < nlines && GP_IN(first + (size_t)(n - 1) * stride, (long long)p.nz * p.ny * (long long)P, p.status)) {
+    E* line = static_cast<E*>(p.psi) + first;
     const E* A = static_cast<const E*>(p.A);
     const E* B = static_cast<const E*>(p.B);
     const E Ab = __ldg(A + n - 1), Bb = __ldg(B + n - 1);

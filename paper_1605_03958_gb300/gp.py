@@ -27,6 +27,7 @@ GP_ERR_CUDA = -3
 GP_ERR_NONFINITE = -4
 GP_ERR_TIMEOUT = -5
 GP_ERR_STATE = -6
+GP_ERR_BOUNDS = -7
 GP_F64 = 0
 GP_F32 = 1
 
@@ -302,6 +303,7 @@ def gp_get_info(h) -> dict:
     d["band_mask"] = (d["fast_mask"] >> 3) & 7
     d["band_w"] = (d["fast_mask"] >> 8) & 15
     d["line64_mask"] = (d["fast_mask"] >> 12) & 7
+    d["x_reg"] = (d["fast_mask"] >> 15) & 1
     d["fast_mask"] &= 7
     return d
 

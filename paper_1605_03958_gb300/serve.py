@@ -1,17 +1,23 @@
 """Continuous-batching server of GP solves over a ``Pool`` (include/gp.h, pools).
 
 Requests (ground-state solves in imaginary time, quench dynamics in real time) are
-admitted into the pool's device arena as they arrive and as room frees up, FIFO;
-every live solve stays resident on the device and all of them advance together in
-quanta of steps (one batched launch per sweep direction and mode per step); a solve
-that has done its steps retires between quanta, its observables are read, and its
-arena range goes to the next waiting request.  A solve's arithmetic does not depend
-on which other solves share the pool, so its result is the same alone and in the mix.
+admitted into the pool's device arena as they arrive and as room frees up: in arrival
+order, except that while the oldest waiting request does not fit, later ones that do
+fit are admitted past it (backfill) until the oldest has waited max_head_wait_s, after
+which admission waits for it.  Every live solve stays resident on the device and all
+of them advance together in quanta of steps (one batched launch per sweep direction
+and mode per step); a solve that has done its steps retires between quanta, its
+observables are read, and its arena range goes to the next waiting request.  A
+request can be cancelled (Server.cancel, or its own cancel_at time) or time out (its
+timeout_s): it then leaves the queue, or the pool between quanta, without a result.
+A solve's arithmetic does not depend on which other solves share the pool, so its
+result is the same alone and in the mix.
 
 The GPU work is the library's; this module only schedules.
 """
 from __future__ import annotations
 
+import threading
 import time
 from collections import deque
 from typing import Callable, Optional
@@ -20,15 +26,20 @@ from .gp import GP_ERR_NOMEM, GPError, Pool
 
 
 class Server:
-    """One pool and a FIFO admission queue.
+    """One pool and an admission queue.
 
     arena_bytes: the pool's arena (default: half of the device's free memory at
     construction, as reported by cudaMemGetInfo through PyTorch); quantum: steps per
-    pool call (a quantum is cut short so that no solve overshoots its step count).
+    pool call (a quantum is cut short so that no solve overshoots its step count);
+    backfill: admit later requests that fit past an oldest one that does not, for at
+    most max_head_wait_s of the oldest one's wait (backfill=False: strict FIFO).
+    Requests may carry timeout_s (latency after which an unfinished request is
+    dropped) and cancel_at (a time, from the start, at which the client cancels it).
     """
 
     def __init__(self, arena_bytes: Optional[int] = None, max_slots: int = 1024,
-                 quantum: int = 100, tune: bool = False):
+                 quantum: int = 100, tune: bool = False, backfill: bool = True,
+                 max_head_wait_s: float = 1.0):
         if arena_bytes is None:
             import torch
             free, _ = torch.cuda.mem_get_info()
@@ -36,8 +47,21 @@ class Server:
         self.pool = Pool(arena_bytes, max_slots)
         self.quantum = int(quantum)
         self.tune = tune
-        self.stats = {"quanta": 0, "steps": 0, "admitted": 0, "max_live": 0,
+        self.backfill = bool(backfill)
+        self.max_head_wait_s = float(max_head_wait_s)
+        self.stats = {"quanta": 0, "steps": 0, "admitted": 0, "max_live": 0, "backfilled": 0,
+                      "cancelled": 0, "timed_out": 0,
                       "step_s": 0.0, "admit_s": 0.0, "retire_s": 0.0, "live_sum": 0}
+        self.cancelled = []               # records of requests dropped without a result
+        self._cancel_ids = set()
+        self._cancel_lock = threading.Lock()
+
+    def cancel(self, request_id) -> None:
+        """Ask for request `request_id` to be dropped: it leaves the queue, or the pool
+        at the next quantum boundary (its slot is freed), without a result.  May be
+        called from another thread or from an on_done callback."""
+        with self._cancel_lock:
+            self._cancel_ids.add(request_id)
 
     def close(self):
         self.pool.close()
@@ -68,30 +92,77 @@ class Server:
             return time.perf_counter() - t0 if realtime else vnow
 
         tuned = not self.tune
+
+        def drop(r, t, why, slot=None):
+            if slot is not None:
+                self.pool.remove(slot)
+            self.cancelled.append({"id": r["id"], "kind": r["kind"], "status": why,
+                                   "arrival": r["arrival"], "dropped": t,
+                                   "steps_done": r["steps"] - r.get("remaining", r["steps"])})
+            self.stats["cancelled" if why == "cancelled" else "timed_out"] += 1
+
+        def reason(r, t):
+            with self._cancel_lock:
+                if r["id"] in self._cancel_ids:
+                    return "cancelled"
+            if r.get("cancel_at") is not None and t >= r["cancel_at"]:
+                return "cancelled"
+            if r.get("timeout_s") is not None and t - r["arrival"] > r["timeout_s"]:
+                return "timeout"
+            return None
+
         while pending or waiting or live:
             t = now()
             while pending and pending[0]["arrival"] <= t:
                 waiting.append(pending.popleft())
+            # cancellations and timeouts, between quanta
+            for r in [r for r in waiting if reason(r, t)]:
+                waiting.remove(r)
+                drop(r, t, reason(r, t))
+            for slot in [s for s, r in live.items() if reason(r, t)]:
+                r = live.pop(slot)
+                drop(r, t, reason(r, t), slot)
             ta = time.perf_counter()
-            while waiting:
+            i = 0
+            while i < len(waiting):
+                r = waiting[i]
                 try:
-                    rec = self._admit(waiting[0], t)
+                    rec = self._admit(r, t)
                 except GPError as e:
-                    if e.code == GP_ERR_NOMEM:
-                        break   # no room until a solve retires
-                    raise
-                waiting.popleft()
+                    if e.code != GP_ERR_NOMEM:
+                        raise
+                    # no room for r: later requests may fit past it while the oldest
+                    # waiting request has not waited too long
+                    head_wait = t - waiting[0]["arrival"]
+                    if not self.backfill or head_wait > self.max_head_wait_s:
+                        break
+                    i += 1
+                    continue
+                del waiting[i]
                 live[rec["slot"]] = rec
                 self.stats["admitted"] += 1
+                if i > 0:
+                    self.stats["backfilled"] += 1
             self.stats["admit_s"] += time.perf_counter() - ta
             if not live:
-                if pending:   # idle until the next arrival
-                    nxt = pending[0]["arrival"]
+                if pending or (waiting and any(r.get("timeout_s") is not None or
+                                               r.get("cancel_at") is not None for r in waiting)):
+                    # idle until the next arrival (or the next deadline of a waiting request)
+                    nxt = pending[0]["arrival"] if pending else float("inf")
+                    for r in waiting:
+                        for d in (r.get("cancel_at"), None if r.get("timeout_s") is None
+                                  else r["arrival"] + r["timeout_s"]):
+                            if d is not None:
+                                nxt = min(nxt, d + 1e-9)
+                    if waiting and not pending and nxt == float("inf"):
+                        raise RuntimeError("a request does not fit the empty pool")
                     if realtime:
                         time.sleep(max(0.0, nxt - now()))
                     else:
                         vnow = max(vnow, nxt)
                     continue
+                if not waiting:
+                    break
                 raise RuntimeError("a request does not fit the empty pool")
             if not tuned:
                 self.pool.tune(3)

@@ -26,7 +26,7 @@ def P():
 
 
 # x rows of 60 (one row per warp at a time) and 16 (grouped rows) 16-byte vectors in
-# FP32 (banded x sweep); the tile kernels (bulk row tiles along x, TMA tiles along y
+# FP32 (the copy-fed banded x sweep); the tile kernels (bulk row tiles along x, TMA tiles along y
 # and z), which FP64 solvers run when GP_SWEEP_KERNELS=tile (their default kernels
 # stream lines through global memory and have no waits)
 CASES = [("f32", (240, 40, 32)), ("f32", (64, 40, 32)), ("f64", (64, 48, 32))]
@@ -37,6 +37,8 @@ CASES = [("f32", (240, 40, 32)), ("f32", (64, 40, 32)), ("f64", (64, 48, 32))]
 def test_wait_that_runs_out_is_reported_and_the_solver_recovers(P, prec, shape, mode, monkeypatch):
     if prec == "f64":
         monkeypatch.setenv("GP_SWEEP_KERNELS", "tile")
+    else:   # the copy-fed banded x sweep (rows of 8 m <= 256 points run without copies)
+        monkeypatch.setenv("GP_X_REG", "0")
     nx, ny, nz = shape
     args = (nx, ny, nz, 0.2, 0.2, 0.2, 0.004, 1.0, 1.41, 2.0)
     s = P.Solver(*args, g=50.0, prec=prec)

@@ -131,3 +131,75 @@ def test_synthetic_request_stream_matches_its_recipe():
         assert p["nz"] % 16 == 0 and 32 <= p["nz"] <= 64
         assert 1.0 <= p["g"] <= 1000.0
     assert workloads.serve_requests(count=50) == workloads.serve_requests(count=50)   # seeded
+
+
+def test_backfill_admits_smaller_requests_past_a_blocked_head(fake):
+    # arena of one 48^3 slot: a 48^3 request waits behind a live 32^3 one, while a later
+    # 32^3 request fits beside it and is admitted past the blocked one
+    srv = serve.Server(arena_bytes=48 ** 3 * 4, quantum=50, max_head_wait_s=10.0)
+    reqs = [req(0, 0.0, 200), req(1, 0.001, 100, n=48), req(2, 0.002, 100)]
+    done = srv.run(reqs, realtime=False, virtual_step_s=1e-3)
+    order = [i for _, i in sorted((d["admitted"], d["id"]) for d in done)]
+    assert order == [0, 2, 1]
+    assert srv.stats["backfilled"] == 1
+    assert all(d["obs"]["steps_done"] == d["steps"] for d in done)
+
+
+def test_head_wait_bound_stops_backfill(fake):
+    # the same stream with no backfill allowed once the head has waited at all
+    srv = serve.Server(arena_bytes=48 ** 3 * 4, quantum=50, max_head_wait_s=0.0)
+    reqs = [req(0, 0.0, 200), req(1, 0.001, 100, n=48), req(2, 0.002, 100)]
+    done = srv.run(reqs, realtime=False, virtual_step_s=1e-3)
+    order = [i for _, i in sorted((d["admitted"], d["id"]) for d in done)]
+    assert order == [0, 1, 2]
+    assert srv.stats["backfilled"] == 0
+
+
+def test_strict_fifo_when_backfill_is_off(fake):
+    srv = serve.Server(arena_bytes=48 ** 3 * 4, quantum=50, backfill=False)
+    reqs = [req(0, 0.0, 200), req(1, 0.001, 100, n=48), req(2, 0.002, 100)]
+    done = srv.run(reqs, realtime=False, virtual_step_s=1e-3)
+    assert [i for _, i in sorted((d["admitted"], d["id"]) for d in done)] == [0, 1, 2]
+
+
+def test_cancelled_live_request_frees_its_slot(fake):
+    # the arena holds one 32^3 slot: request 0 is cancelled while live (at t = 0.05 s of
+    # virtual time, 50 of its 1000 steps done), its slot goes to request 1
+    srv = serve.Server(arena_bytes=32 ** 3 * 4, quantum=50)
+    r0 = dict(req(0, 0.0, 1000), cancel_at=0.05)
+    done = srv.run([r0, req(1, 0.0, 100)], realtime=False, virtual_step_s=1e-3)
+    assert [d["id"] for d in done] == [1]
+    (c,) = srv.cancelled
+    assert c["id"] == 0 and c["status"] == "cancelled" and c["steps_done"] == 50
+    removes = [x for x in srv.pool.calls if x[0] == "remove"]
+    assert removes[0] == ("remove", 0)            # freed before request 1 was admitted
+    assert srv.pool.calls.index(removes[0]) < srv.pool.calls.index(("add", 1))
+    assert srv.stats["cancelled"] == 1 and not srv.pool.live
+
+
+def test_cancelled_waiting_request_is_never_admitted(fake):
+    srv = serve.Server(arena_bytes=32 ** 3 * 4, quantum=50)
+    done = srv.run([req(0, 0.0, 200), dict(req(1, 0.0, 100), cancel_at=0.1), req(2, 0.0, 100)],
+                   realtime=False, virtual_step_s=1e-3)
+    assert sorted(d["id"] for d in done) == [0, 2]
+    assert [c["id"] for c in srv.cancelled] == [1] and srv.cancelled[0]["steps_done"] == 0
+    assert len([x for x in srv.pool.calls if x[0] == "add"]) == 2   # requests 0 and 2 only
+
+
+def test_request_timeout_drops_an_unfinished_solve(fake):
+    srv = serve.Server(arena_bytes=1 << 30, quantum=100)
+    done = srv.run([dict(req(0, 0.0, 5000), timeout_s=0.25), req(1, 0.0, 300)],
+                   realtime=False, virtual_step_s=1e-3)
+    assert [d["id"] for d in done] == [1]
+    (c,) = srv.cancelled
+    assert c["id"] == 0 and c["status"] == "timeout" and 0 < c["steps_done"] < 5000
+    assert srv.stats["timed_out"] == 1 and not srv.pool.live
+
+
+def test_cancel_from_a_callback(fake):
+    # a client cancels request 2 when request 0 finishes
+    srv = serve.Server(arena_bytes=1 << 30, quantum=100)
+    done = srv.run([req(0, 0.0, 100), req(1, 0.0, 300), req(2, 0.0, 1000)], realtime=False,
+                   virtual_step_s=1e-3, on_done=lambda d: d["id"] == 0 and srv.cancel(2))
+    assert sorted(d["id"] for d in done) == [0, 1]
+    assert [c["id"] for c in srv.cancelled] == [2] and srv.cancelled[0]["steps_done"] == 100
