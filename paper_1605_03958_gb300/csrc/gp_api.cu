@@ -244,6 +244,12 @@ bool force_tile() {
   const char* v = std::getenv("GP_SWEEP_KERNELS");
   return v && std::strcmp(v, "tile") == 0;
 }
+// GP_NORM_DEFER=0 makes the FP32 banded z sweep finish its norm itself (last block)
+// instead of leaving the sum of its partials to the next x sweep (A/B measurements).
+bool norm_defer_enabled() {
+  const char* v = std::getenv("GP_NORM_DEFER");
+  return !(v && std::strcmp(v, "0") == 0);
+}
 // GP_X_REG=0 keeps the banded x sweep on the copy-fed kernel for rows that the
 // register-row kernel could take (A/B measurements).
 bool x_reg_enabled() {
@@ -311,6 +317,8 @@ struct gp_solver {
   int fast_grid[2][3] = {};          // blocks of the fast sweeps (x band: persistent grid)
   int band_w[2][3] = {};             // FP32 banded sweep half-width per mode and axis, 0 = not used
   bool line64 = false;               // FP64 field: the line-streaming sweeps of gp_sweeps64.cu
+  bool defer_norm = false;           // FP32 real field: the z sweep's norm finished by its reader
+  int* scale_state = nullptr;        // device: 1 while the factor is in the z sweep's partials
   int split = GP_SPLIT_LIE;          // splitting of a step
   bool kinetic_only = false;         // x sweep without the pointwise substep (Strang)
   float band_wt[2][3][2 * 17] = {};  // its weights (complex: pairs)
@@ -352,7 +360,21 @@ int cuda_fail(gp_solver* s, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
   } while (0)
 
+// The factor of a solver whose z sweep defers its norm: sum the partials into it when
+// they are newer than it (one small kernel on the solver's stream; nothing otherwise).
+void resolve_scale(gp_solver* s) {
+  if (!s->defer_norm) return;
+  const cudaError_t e =
+      gpk::launch_resolve_scale(s->scale, s->scale_state, s->partials,
+                                (int)s->fast_grid[0][2], s->prm.dx * s->prm.dy * s->prm.dz,
+                                s->status, s->stream);
+  if (e != cudaSuccess) cuda_fail(s, e, "resolve scale");
+}
+
+// Arguments of the reductions, I/O and pointwise kernels, which all read the pending
+// factor: a deferred one is resolved first.
 FieldParams field_params(gp_solver* s) {
+  resolve_scale(s);
   FieldParams f;
   f.psi = s->field;
   f.nx = s->prm.nx;
@@ -560,6 +582,19 @@ void fill_sweep_params(gp_solver* s) {
         s->fast_grid[m][a] = (int)blocks;
       }
     }
+  // FP32 real field, banded x and z sweeps: the z sweep only stores its norm partials
+  // and the next x sweep sums them (every block, in the same order) into the factor it
+  // applies, instead of the last z block summing them at the end of the z sweep; other
+  // readers of the factor resolve it first (resolve_scale)
+  s->defer_norm = s->L.rbytes == 4 && p.nz > 1 && s->band_w[0][0] && s->band_w[0][2] &&
+                  norm_defer_enabled();
+  for (int a = 0; a < 3; ++a) {
+    SweepParams& q = s->sp[0][a];
+    q.norm_defer = s->defer_norm && a != 1 ? 1 : 0;
+    q.norm_blocks = s->fast_grid[0][2];
+    q.norm_copies = std::max(1, std::min(8, (int)(s->L.npartials / std::max(1, s->fast_grid[0][2]))));
+    q.scale_state = s->scale_state;
+  }
 }
 
 template <class T> void put(std::vector<unsigned char>& buf, size_t off, const T& v) {
@@ -703,10 +738,13 @@ int upload_tables(gp_solver* s) {
   return GP_OK;
 }
 
-__global__ void k_set_double(double* p, double v) { *p = v; }
+__global__ void k_set_scale_one(double* scale, int* state) {
+  *scale = 1.0;
+  *state = 0;
+}
 
 int set_scale_one(gp_solver* s) {
-  k_set_double<<<1, 1, 0, s->stream>>>(s->scale, 1.0);
+  k_set_scale_one<<<1, 1, 0, s->stream>>>(s->scale, s->scale_state);
   GP_CUDA(s, cudaGetLastError());
   return GP_OK;
 }
@@ -765,6 +803,7 @@ int create_impl(const gp_params* p, void* dev_buf, size_t bytes, void* stream, g
   s->scale = reinterpret_cast<double*>(sc);
   s->obs = reinterpret_cast<double*>(sc + 64);
   s->status = reinterpret_cast<int*>(sc + 256);
+  s->scale_state = reinterpret_cast<int*>(sc + 160);
   s->counters = reinterpret_cast<unsigned int*>(sc + 320);
 
   int rc = GP_OK;
@@ -1402,6 +1441,7 @@ int gp_density1d(gp_solver* s, int axis, double* out) {
 int gp_sync(gp_solver* s) {
   if (!s) return GP_ERR_ARG;
   wait_copies(s);
+  resolve_scale(s);   // a deferred norm's non-finite flag is set where it is summed
   return check_status(s);
 }
 

@@ -329,6 +329,45 @@ __device__ __forceinline__ void norm_finish_ff(FF acc, FF* partials, unsigned in
     for (unsigned int g = threadIdx.x; g < ngroups; g += blockDim.x) gcounter[g] = 0u;
 }
 
+// Fixed-order block sum of the nb float-float partials of a deferred norm, the same
+// bits in every block of every kernel that takes it: thread t adds partials t, t + T,
+// ... (all its loads in flight together), then the warp shuffle tree, then the warps
+// in order.  Every thread of the block must call it; all get the factor
+// 1 / sqrt(dV sum), formed in FP32 (it scales an FP32 field; rsqrtf is within 2 ulp,
+// and the factor is remeasured every step, so its error does not accumulate), and the
+// block's thread 0 flags a non-finite or zero norm when flag is set.
+__device__ __forceinline__ double deferred_scale(const double* partials, int nb, double dV,
+                                                 int* status, bool flag) {
+  __shared__ FF wsum[32];
+  __shared__ double result;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned int T = blockDim.x;
+  FF s = FF{0.f, 0.f};
+  for (unsigned int t0 = threadIdx.x; t0 < (unsigned int)nb; t0 += 8 * T) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const unsigned int t = t0 + q * T;
+      v[q] = t < (unsigned int)nb ? __ldcg(reinterpret_cast<const float2*>(partials) + t)
+                                  : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = ff_add(s, FF{v[q].x, v[q].y});
+  }
+  for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_down(s, o));
+  if (lane == 0) wsum[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    FF b = wsum[0];
+    for (int w = 1; w < nw; ++w) b = ff_add(b, wsum[w]);
+    const float norm = (b.hi + b.lo) * (float)dV;
+    if (flag && (!(norm > 0.f) || !isfinite(norm))) atomicOr(status, kStatusNonFinite);
+    result = (double)rsqrtf(norm);
+  }
+  __syncthreads();
+  return result;
+}
+
 // ------------------------------------------------------------------- arithmetic
 
 template <class R> struct Cplx;

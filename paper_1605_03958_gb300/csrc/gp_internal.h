@@ -97,6 +97,15 @@ struct SweepParams {
   double* partials;
   unsigned int* counter;
   double* scale_out;
+  // deferred finish of the fused norm (FP32 real field): the z sweep stores its
+  // per-block partials (norm_blocks of them) and sets *scale_state = 1; the next x
+  // sweep (every block, the same fixed order) sums them into the factor it applies,
+  // and any other reader of the factor first runs k_resolve_scale
+  int norm_defer;        // z: store partials only; x: take the factor from the partials
+  int norm_blocks;       // blocks of the z sweep (partials to sum)
+  int norm_copies;       // z stores norm_copies copies of its partials (copy c at c norm_blocks);
+                         // x block b reads copy b mod norm_copies: fewer readers per L2 line
+  int* scale_state;      // 1: the factor is the partials' 1 / sqrt(sum dV)
   int* status;
   double dV;
   long long ntiles;
@@ -219,6 +228,10 @@ template <class R> cudaError_t launch_half_pointwise(const FieldParams& p, bool 
                                                      const void* fx, const void* fyz, double dtg,
                                                      bool apply_scale, bool norm, cudaStream_t st);
 template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaStream_t st);
+// When *state is 1: the factor 1 / sqrt(dV sum of the nb float-float partials) into
+// *scale (non-finite or zero norm flagged in *status), and *state = 0 (one block).
+cudaError_t launch_resolve_scale(double* scale, int* state, const double* partials, int nb,
+                                 double dV, int* status, cudaStream_t st);
 // psi <- *p.scale psi in place (the caller then sets the factor to 1).
 template <class R> cudaError_t launch_fold_scale(const FieldParams& p, bool complex_field,
                                                  cudaStream_t st);

@@ -416,6 +416,22 @@ cudaError_t launch_observables(const FieldParams& p, bool complex_field, cudaStr
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_resolve_scale(double* scale, int* state, const double* partials,
+                                                      int nb, double dV, int* status) {
+  if (*state == 0) return;   // uniform: every thread reads the same word
+  const double f = deferred_scale(partials, nb, dV, status, true);
+  if (threadIdx.x == 0) {
+    *scale = f;
+    *state = 0;
+  }
+}
+
+cudaError_t launch_resolve_scale(double* scale, int* state, const double* partials, int nb,
+                                 double dV, int* status, cudaStream_t st) {
+  k_resolve_scale<<<1, 256, 0, st>>>(scale, state, partials, nb, dV, status);
+  return cudaGetLastError();
+}
+
 template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaStream_t st) {
   k_norm_to_scale<R><<<kReduceBlocks, kReduceThreads, 0, st>>>(p);
   return cudaGetLastError();

@@ -1023,13 +1023,22 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   const int nrow = (int)max(0LL, min((long long)p.band_rows, nrows - row0));
   x_band_init(full, slots, S, S * G, slot_elems);
   pdl_begin();
+  // the pending factor (see k_sweep_x_reg), for every warp of the block
+  __shared__ double s_factor;
+  const bool defer = p.norm_defer && *p.scale_state;
+  if (defer) {
+    const double f = deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks, p.norm_blocks, p.dV,
+                                    p.status, blockIdx.x == 0);
+    if (threadIdx.x == 0) s_factor = f;
+    __syncthreads();
+  }
   if (nrow == 0) return;
   XRows<E> a;
   a.field = static_cast<E*>(p.psi);
   a.fx = static_cast<const float4*>(p.band_fx);
   a.fyz = static_cast<const E*>(p.band_fyz);
   a.wt = reinterpret_cast<const E*>(p.band_wt);
-  a.scale = p.scale;
+  a.scale = defer ? &s_factor : p.scale;
   a.status = p.status;
   a.wait_ns = p.wait_ns;
   a.row0 = row0;
@@ -1085,8 +1094,6 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_co
     }
   }
   pdl_begin();
-  if (nrow == 0) return;
-  const float s = (float)(*p.scale);
   const float dtg = p.band_dtg;
   const bool pw = p.pw != 0;
   E* field = static_cast<E*>(p.psi);
@@ -1099,6 +1106,7 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_co
       buf[q] = act && GP_IN(r * pitch + x0 + (q + 1) * EPT - 1, nel, p.status)
                    ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
   };
+  float s = 1.f;   // the pending factor, set below once the first row's loads are out
   // row r's pointwise substep, banded operator and store, from its loaded vectors
   auto process = [&](long long r, const float4 (&cur)[VPL], E fr) {
     E v[8];
@@ -1151,10 +1159,21 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_co
     }
   };
   // the next row's loads are in flight while a row is processed (deeper prefetch,
-  // in registers or through shared memory, measured slower at 240 x 200 x 160)
+  // in registers or through shared memory, measured slower at 240 x 200 x 160);
+  // the first row's loads go out before the pending factor is known: it is stored, or
+  // summed from the previous z sweep's partials (every block the same bits; all
+  // threads take part before any warp may leave)
   float4 cur[VPL], nxt[VPL];
-  load_row(row0, cur);
-  E fr = fyz[row0];
+  E fr = F::zero();
+  if (nrow > 0) {
+    load_row(row0, cur);
+    fr = fyz[row0];
+  }
+  s = (float)(p.norm_defer && *p.scale_state
+                   ? deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks, p.norm_blocks, p.dV,
+                                    p.status, blockIdx.x == 0)
+                   : *p.scale);
+  if (nrow == 0) return;
   for (int i = 0; i < nrow; ++i) {
     const long long r = row0 + i;
     E frn = fr;
@@ -1460,9 +1479,26 @@ __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__
   } else {
     acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, t);
   }
-  if (NORM)
-    norm_finish_ff(acc, reinterpret_cast<FF*>(p.partials), p.counter, gridDim.x, blockIdx.x,
-                   p.scale_out, p.status, p.dV, p.counter + kNormGroupBase, kNormGroups);
+  if (NORM) {
+    if (p.norm_defer) {
+      // the partial only; the next reader of the factor sums the partials
+      __shared__ FF wdef[32];
+      FF b = acc;
+      for (int o = 16; o > 0; o >>= 1) b = ff_add(b, ff_shfl_down(b, o));
+      if ((threadIdx.x & 31) == 0) wdef[threadIdx.x >> 5] = b;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        FF s = wdef[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = ff_add(s, wdef[w]);
+        for (int c = 0; c < p.norm_copies; ++c)
+          reinterpret_cast<FF*>(p.partials)[(size_t)c * gridDim.x + blockIdx.x] = s;
+        if (blockIdx.x == 0) *p.scale_state = 1;
+      }
+    } else {
+      norm_finish_ff(acc, reinterpret_cast<FF*>(p.partials), p.counter, gridDim.x, blockIdx.x,
+                     p.scale_out, p.status, p.dV, p.counter + kNormGroupBase, kNormGroups);
+    }
+  }
 }
 
 // Batched y / z sweep: block b of the launch is block blk of nblk of one slot; the
