@@ -161,7 +161,7 @@ def source_hash():
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("gp_sweeps.cu", "gp_device.cuh", "gp_internal.h", "gp_api.cu"):
+    for f in ("gp_sweeps.cu", "gp_sweeps64.cu", "gp_device.cuh", "gp_internal.h", "gp_api.cu"):
         with open(os.path.join(ROOT, "paper_1605_03958_gb300", "csrc", f)) as fh:
             code = fh.read()
         code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)

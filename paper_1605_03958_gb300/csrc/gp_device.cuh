@@ -196,7 +196,7 @@ __device__ __forceinline__ double sum_fixed(const double* w, int n) {
 __device__ __forceinline__ void norm_finish(double acc, double* partials, unsigned int* counter,
                                             unsigned int nb, unsigned int bid, double* scale_out,
                                             int* status, double dV) {
-  __shared__ double wpart[32];
+  __shared__ double wpart[kMaxBlockWarps];
   __shared__ int last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -271,12 +271,13 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p) {
 // hundreds of blocks finishing together otherwise queue on one address at the L2.
 // The acquire-release tickets chain, so the last block sees every partial.  The last
 // block resets every counter it used.
+// wpart_ff: shared memory for kMaxBlockWarps FF values and one int (a kernel may pass
+// dynamic shared memory it no longer needs, behind a barrier).
 __device__ __forceinline__ void norm_finish_ff(FF acc, FF* partials, unsigned int* counter,
                                                unsigned int nb, unsigned int bid, double* scale_out,
-                                               int* status, double dV,
-                                               unsigned int* gcounter = nullptr, int G = 1) {
-  __shared__ FF wpart_ff[32];
-  __shared__ int last_ff;
+                                               int* status, double dV, unsigned int* gcounter,
+                                               int G, FF* wpart_ff) {
+  int& last_ff = *reinterpret_cast<int*>(wpart_ff + kMaxBlockWarps);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int o = 16; o > 0; o >>= 1) acc = ff_add(acc, ff_shfl_down(acc, o));
   if (lane == 0) wpart_ff[warp] = acc;
@@ -337,9 +338,14 @@ __device__ __forceinline__ void norm_finish_ff(FF acc, FF* partials, unsigned in
 // and the factor is remeasured every step, so its error does not accumulate), and the
 // block's thread 0 flags a non-finite or zero norm when flag is set.
 __device__ __forceinline__ double deferred_scale(const double* partials, int nb, double dV,
-                                                 int* status, bool flag) {
-  __shared__ FF wsum[32];
+                                                 int* status, bool flag, const int* state = nullptr,
+                                                 const double* stored = nullptr) {
+  __shared__ FF wsum[kMaxBlockWarps];
   __shared__ double result;
+  // with `state`: the partials are read whatever it holds (they are always valid memory)
+  // so that its load and theirs are in flight together; the result is the partials'
+  // factor when *state is 1 and *stored otherwise
+  const int st = state ? *state : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned int T = blockDim.x;
   FF s = FF{0.f, 0.f};
@@ -361,8 +367,12 @@ __device__ __forceinline__ double deferred_scale(const double* partials, int nb,
     FF b = wsum[0];
     for (int w = 1; w < nw; ++w) b = ff_add(b, wsum[w]);
     const float norm = (b.hi + b.lo) * (float)dV;
-    if (flag && (!(norm > 0.f) || !isfinite(norm))) atomicOr(status, kStatusNonFinite);
-    result = (double)rsqrtf(norm);
+    if (st) {
+      if (flag && (!(norm > 0.f) || !isfinite(norm))) atomicOr(status, kStatusNonFinite);
+      result = (double)rsqrtf(norm);
+    } else {
+      result = *stored;
+    }
   }
   __syncthreads();
   return result;

@@ -39,6 +39,12 @@ constexpr int kBatchXWarps = 4;
 // Largest half-width of the banded operators (weights arrays hold 2 kBandHalfMax + 1).
 constexpr int kBandHalfMax = 8;
 
+// Most warps per block of any kernel that ends with a block-level norm reduction (the
+// per-warp arrays of those reductions are sized by it; their blocks have 4 to 12
+// warps).  Small static arrays matter: the banded y / z blocks take 45 KB of dynamic
+// shared memory each, five to an SM, with little room to spare.
+constexpr int kMaxBlockWarps = 16;
+
 // Ticket counters of the fused norm: a solver's counters[0] is the top counter,
 // counters[kNormGroupBase .. + kNormGroups) the group counters (the solver's scalar
 // area holds 48 counters).

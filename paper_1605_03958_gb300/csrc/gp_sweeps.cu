@@ -1025,10 +1025,10 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   pdl_begin();
   // the pending factor (see k_sweep_x_reg), for every warp of the block
   __shared__ double s_factor;
-  const bool defer = p.norm_defer && *p.scale_state;
+  const bool defer = p.norm_defer != 0;
   if (defer) {
-    const double f = deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks, p.norm_blocks, p.dV,
-                                    p.status, blockIdx.x == 0);
+    const double f = deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks,
+                                    p.norm_blocks, p.dV, p.status, blockIdx.x == 0, p.scale_state, p.scale);
     if (threadIdx.x == 0) s_factor = f;
     __syncthreads();
   }
@@ -1169,9 +1169,9 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_co
     load_row(row0, cur);
     fr = fyz[row0];
   }
-  s = (float)(p.norm_defer && *p.scale_state
-                   ? deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks, p.norm_blocks, p.dV,
-                                    p.status, blockIdx.x == 0)
+  s = (float)(p.norm_defer
+                   ? deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks,
+                                    p.norm_blocks, p.dV, p.status, blockIdx.x == 0, p.scale_state, p.scale)
                    : *p.scale);
   if (nrow == 0) return;
   for (int i = 0; i < nrow; ++i) {
@@ -1480,9 +1480,22 @@ __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__
     acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, t);
   }
   if (NORM) {
+    // the block's per-warp sums in shared memory: the cp.async slots when the kernel
+    // has them (idle now: every thread has waited for its copies and the barrier
+    // orders their last reads), so that the kernel keeps no static shared memory and
+    // five 45 KB blocks fit an SM
+    FF* wsh;
+    if constexpr (CP) {
+      extern __shared__ __align__(16) float4 band_slots[];
+      __syncthreads();
+      wsh = reinterpret_cast<FF*>(band_slots);
+    } else {
+      __shared__ FF wsh_static[kMaxBlockWarps + 1];
+      wsh = wsh_static;
+    }
     if (p.norm_defer) {
       // the partial only; the next reader of the factor sums the partials
-      __shared__ FF wdef[32];
+      FF* wdef = wsh;
       FF b = acc;
       for (int o = 16; o > 0; o >>= 1) b = ff_add(b, ff_shfl_down(b, o));
       if ((threadIdx.x & 31) == 0) wdef[threadIdx.x >> 5] = b;
@@ -1496,7 +1509,7 @@ __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__
       }
     } else {
       norm_finish_ff(acc, reinterpret_cast<FF*>(p.partials), p.counter, gridDim.x, blockIdx.x,
-                     p.scale_out, p.status, p.dV, p.counter + kNormGroupBase, kNormGroups);
+                     p.scale_out, p.status, p.dV, p.counter + kNormGroupBase, kNormGroups, wsh);
     }
   }
 }
@@ -1521,9 +1534,11 @@ __global__ void __launch_bounds__(128) k_batch_band_line(const __grid_constant__
   a.Ls = d.seg[AXIS];
   a.status = b.status;
   const FF acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, (long long)lb.blk * blockDim.x + threadIdx.x);
-  if (NORM)
+  if (NORM) {
+    __shared__ FF wsh[kMaxBlockWarps + 1];
     norm_finish_ff(acc, reinterpret_cast<FF*>(d.partials), d.counter, (unsigned int)lb.nblk,
-                   (unsigned int)lb.blk, d.scale, b.status, d.dV);
+                   (unsigned int)lb.blk, d.scale, b.status, d.dV, nullptr, 1, wsh);
+  }
 }
 
 // ---------------------------------------------------------------- launchers
