@@ -56,7 +56,7 @@ def test_source_hash_ignores_comments_and_follows_code(tmp_path, monkeypatch):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     csrc = os.path.join(tmp_path, "paper_1605_03958_gb300", "csrc")
     os.makedirs(csrc)
-    for f in ("gp_sweeps.cu", "gp_device.cuh", "gp_internal.h", "gp_api.cu"):
+    for f in ("gp_sweeps.cu", "gp_sweeps64.cu", "gp_device.cuh", "gp_internal.h", "gp_api.cu"):
         shutil.copy(os.path.join(root, "paper_1605_03958_gb300", "csrc", f), csrc)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench.source_hash()
