@@ -1533,11 +1533,15 @@ __global__ void __launch_bounds__(128) k_batch_band_line(const __grid_constant__
   a.pitch = d.pitch;
   a.Ls = d.seg[AXIS];
   a.status = b.status;
-  const FF acc = band_line_thread<R, CPLX, AXIS, NORM, W>(a, (long long)lb.blk * blockDim.x + threadIdx.x);
+  // the next turn's inputs copied to shared memory ahead, as in k_sweep_band_line
+  extern __shared__ __align__(16) float4 band_slots[];
+  const FF acc = band_line_thread_cp<R, CPLX, AXIS, NORM, W>(a, (long long)lb.blk * blockDim.x + threadIdx.x,
+                                                             band_slots);
   if (NORM) {
-    __shared__ FF wsh[kMaxBlockWarps + 1];
+    __syncthreads();   // the slots are idle now: the norm's per-warp sums go there
     norm_finish_ff(acc, reinterpret_cast<FF*>(d.partials), d.counter, (unsigned int)lb.nblk,
-                   (unsigned int)lb.blk, d.scale, b.status, d.dV, nullptr, 1, wsh);
+                   (unsigned int)lb.blk, d.scale, b.status, d.dV, nullptr, 1,
+                   reinterpret_cast<FF*>(band_slots));
   }
 }
 
@@ -1757,10 +1761,27 @@ size_t batch_x_smem(int stages, int group_max, int slot_elems, bool complex_fiel
          (size_t)kBatchXWarps * stages * group_max * slot_elems * (complex_field ? 8 : 4);
 }
 
+// the batched y / z kernels' turn slots (above 48 KB at W = 8), every mode and axis
+template <int W> static cudaError_t batch_yz_prepare() {
+  void (*const yz[4])(BatchArgs) = {k_batch_band_line<float, false, 1, false, W>,
+                                    k_batch_band_line<float, false, 2, true, W>,
+                                    k_batch_band_line<float, true, 1, false, W>,
+                                    k_batch_band_line<float, true, 2, false, W>};
+  for (auto k : yz) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)band_line_smem(W, true));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <int W> static cudaError_t batch_prepare_W(bool cplx, size_t x_smem, int* bps) {
   void (*k)(BatchArgs) = cplx ? k_batch_x_band<float, true, W> : k_batch_x_band<float, false, W>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x_smem);
   if (e != cudaSuccess) return e;
+  if ((e = batch_yz_prepare<3>()) != cudaSuccess || (e = batch_yz_prepare<5>()) != cudaSuccess ||
+      (e = batch_yz_prepare<8>()) != cudaSuccess)
+    return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, 32 * kBatchXWarps, x_smem);
 }
 
@@ -1779,11 +1800,12 @@ static cudaError_t launch_batch_W(int axis, const BatchArgs& b, bool cplx, int g
   if (axis == 0)
     return cplx ? launch_pdl(k_batch_x_band<float, true, W>, grid, 32 * kBatchXWarps, smem, st, b)
                 : launch_pdl(k_batch_x_band<float, false, W>, grid, 32 * kBatchXWarps, smem, st, b);
+  const size_t ysmem = band_line_smem(W, true);
   if (axis == 1)
-    return cplx ? launch_pdl(k_batch_band_line<float, true, 1, false, W>, grid, 128, 0, st, b)
-                : launch_pdl(k_batch_band_line<float, false, 1, false, W>, grid, 128, 0, st, b);
-  return cplx ? launch_pdl(k_batch_band_line<float, true, 2, false, W>, grid, 128, 0, st, b)
-              : launch_pdl(k_batch_band_line<float, false, 2, true, W>, grid, 128, 0, st, b);
+    return cplx ? launch_pdl(k_batch_band_line<float, true, 1, false, W>, grid, 128, ysmem, st, b)
+                : launch_pdl(k_batch_band_line<float, false, 1, false, W>, grid, 128, ysmem, st, b);
+  return cplx ? launch_pdl(k_batch_band_line<float, true, 2, false, W>, grid, 128, ysmem, st, b)
+              : launch_pdl(k_batch_band_line<float, false, 2, true, W>, grid, 128, ysmem, st, b);
 }
 
 cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,
