@@ -364,8 +364,9 @@ int gp_pool_tune(gp_pool* pool, int steps_per_candidate, double* best_ms);
 int gp_pool_set_graph(gp_pool* pool, int enable);
 
 /* info[0] live slots, [1] arena bytes in use, [2] x_stages, [3] seg_turns,
- * [4] 1 when a step graph is instantiated, [5] launches per step, [6] free arena
- * bytes, [7] largest free range.                                                  */
+ * [4] bit 0: a step graph is instantiated, bit 1: the imaginary-time slots' x sweep
+ * holds each row in registers (every such slot has rows of 16 m <= 512 points), [5]
+ * launches per step, [6] free arena bytes, [7] largest free range.                */
 int gp_pool_info(const gp_pool* pool, long long info[8]);
 const char* gp_pool_last_error(const gp_pool* pool);
 

@@ -125,6 +125,7 @@ struct gp_pool {
   int slot_elems[2] = {};      // x: shared-memory row slot per mode
   size_t x_smem[2] = {};
   int x_stages_used[2] = {2, 2};
+  bool x_reg[2] = {false, false};    // x sweep with rows in registers for the mode's slots
   int x_group_max[2] = {1, 1};
   int live_mode[2] = {};       // live slots per mode
   // launch shape (autotuned)
@@ -159,6 +160,12 @@ int pcuda(gp_pool* P, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return pcuda((P), e_, #call); \
   } while (0)
+
+// GP_X_REG=0 keeps the pools' x sweeps on the copy-fed kernel (A/B measurements).
+bool batch_x_reg_enabled() {
+  const char* v = std::getenv("GP_X_REG");
+  return !(v && std::strcmp(v, "0") == 0);
+}
 
 bool slot_ok(const gp_pool* P, int slot) {
   return P && slot >= 0 && slot < (int)P->slots.size() && P->slots[slot].live;
@@ -321,6 +328,18 @@ int rebuild(gp_pool* P) {
     }
     // x: stages that fit shared memory, rows per group per slot, rows per warp such
     // that every warp is resident at once
+    // real slots whose rows are 16 m <= 512 points at a half-width of 3 or 5: rows in
+    // registers, floor(32 / (nx / 16)) rows of a slot per warp pass
+    bool reg = !cplx && (P->wl[m][0] == 3 || P->wl[m][0] == 5) && batch_x_reg_enabled();
+    for (int i = 0; i < ns && reg; ++i)
+      if (P->slots[i].live && P->slots[i].mode == m)
+        reg = P->slots[i].prm.nx % 16 == 0 && P->slots[i].prm.nx <= 512;
+    int rbps = 0;
+    if (reg && (gpk::batch_x_reg_prepare(P->wl[m][0], &rbps) != cudaSuccess || rbps <= 0)) {
+      cudaGetLastError();
+      reg = false;
+    }
+    P->x_reg[m] = reg;
     int st = P->x_stages;
     while (st > 2 && gpk::batch_x_smem(st, 1, P->slot_elems[m], cplx) > kMaxSmem) --st;
     P->x_stages_used[m] = st;
@@ -346,7 +365,8 @@ int rebuild(gp_pool* P) {
     for (int i = 0; i < ns; ++i)
       if (P->slots[i].live && P->slots[i].mode == m)
         rows_tot += (long long)P->slots[i].prm.ny * P->slots[i].prm.nz;
-    const long long cap = (long long)P->nsm * bps * gpk::kBatchXWarps;
+    const long long cap = reg ? (long long)P->nsm * rbps * gpk::kXRegWarps
+                              : (long long)P->nsm * bps * gpk::kBatchXWarps;
     const int rpw = (int)std::max<long long>(1, (rows_tot + cap - 1) / cap);
     std::vector<XItem> xi;
     std::vector<LineBlock> lb[3];
@@ -354,12 +374,15 @@ int rebuild(gp_pool* P) {
       const Slot& S = P->slots[i];
       if (!S.live || S.mode != m) continue;
       const long long rows = (long long)S.prm.ny * S.prm.nz;
-      for (long long r = 0; r < rows; r += rpw) {
+      // register rows: items of a whole number of passes of rp rows each
+      const int rp = reg ? std::max(1, 32 / (S.prm.nx / 16)) : 1;
+      const int ipw = reg ? (rpw + rp - 1) / rp * rp : rpw;
+      for (long long r = 0; r < rows; r += ipw) {
         XItem it;
         it.slot = i;
         it.row0 = r;
-        it.nrow = (int)std::min<long long>(rpw, rows - r);
-        it.group = grp[i];
+        it.nrow = (int)std::min<long long>(ipw, rows - r);
+        it.group = reg ? rp : grp[i];
         it.pad = 0;
         xi.push_back(it);
       }
@@ -411,9 +434,11 @@ int launch_step(gp_pool* P) {
       b.slot_elems = P->slot_elems[m];
       b.status = P->d_status;
       b.wait_ns = gpk::kWaitLimitNs;
-      const int grid = a == 0 ? (b.nitems + gpk::kBatchXWarps - 1) / gpk::kBatchXWarps : b.nitems;
+      b.x_reg = P->x_reg[m] ? 1 : 0;
+      const int xw = b.x_reg ? gpk::kXRegWarps : gpk::kBatchXWarps;
+      const int grid = a == 0 ? (b.nitems + xw - 1) / xw : b.nitems;
       const cudaError_t e = gpk::launch_batch_sweep(a, P->wl[m][a], b, m == 1, grid,
-                                                    a == 0 ? P->x_smem[m] : 0, P->stream);
+                                                    a == 0 && !b.x_reg ? P->x_smem[m] : 0, P->stream);
       if (e != cudaSuccess) return pcuda(P, e, "batched sweep launch");
     }
   }
@@ -796,7 +821,7 @@ int gp_pool_info(const gp_pool* P, long long info[8]) {
   info[1] = (long long)(P->capacity - P->alloc.free_total());
   info[2] = P->x_stages;
   info[3] = P->seg_turns;
-  info[4] = P->exec ? 1 : 0;
+  info[4] = (P->exec ? 1 : 0) | (P->x_reg[0] ? 2 : 0);
   info[5] = P->launches_per_step;
   info[6] = (long long)P->alloc.free_total();
   info[7] = (long long)P->alloc.largest();

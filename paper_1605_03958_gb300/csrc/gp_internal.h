@@ -160,6 +160,7 @@ struct BatchArgs {
   int slot_elems;         // x: shared-memory row slot, elements (>= pitch + 16 of every slot)
   int* status;
   unsigned long long wait_ns;   // limit of the first bounded wait on each copy
+  int x_reg;              // x: rows in registers (k_batch_x_reg), items of `group` rows per pass
 };
 
 // Arguments of the reductions and conversion kernels.
@@ -213,6 +214,9 @@ int x_band_group(int nx, int ept, int stages, size_t slot_bytes, size_t warp_bud
 cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_blocks_per_sm);
 cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,
                                size_t smem, cudaStream_t st);
+// Batched x sweep with rows in registers (real slots of nx = 16 m <= 512, W in {3, 5}):
+// resident blocks of kXRegWarps warps per SM.
+cudaError_t batch_x_reg_prepare(int w, int* blocks_per_sm);
 // FP64 sweeps (gp_sweeps64.cu): x moves 32 rows per warp through shared-memory
 // chunks (dynamic shared memory x64_smem), y / z stream one line per thread; the
 // launch covers the whole grid (sweep64_blocks blocks).  sweep64_prepare sets the x

@@ -1225,6 +1225,129 @@ __global__ void __launch_bounds__(32 * kBatchXWarps) k_batch_x_band(const __grid
   x_band_rows<R, CPLX, W>(a, full, slots);
 }
 
+// Batched x sweep with rows in registers, for real fields whose every live slot has
+// rows of nx = 16 m <= 512 points (half-width W <= 7): lane li of a row owns its
+// sixteen elements [16 li, 16 li + 16) (four 16-byte vectors).  Warp w takes work item
+// w, it.nrow consecutive rows of one slot, it.group = floor(32 / L) rows at a time
+// (L = nx / 16 lanes per row; rows of 32-160 points fill 27-32 lanes); the next pass's
+// rows in flight while a pass is processed.  Per row as in k_sweep_x_reg: pending
+// factor and pointwise substep in registers, the W neighbours by shuffles from lanes
+// li -/+ 1, odd images at the row's own first and last lanes; the pointwise polynomial
+// is chosen per row (a ballot over the row's lanes), so a slot's arithmetic does not
+// depend on which rows share a warp.
+template <int W>
+__global__ void __launch_bounds__(32 * kXRegWarps) k_batch_x_reg(const __grid_constant__ BatchArgs b) {
+  using F = Field<float, false>;
+  constexpr int EPL = 16, VPL = 4;
+  static_assert(W <= 7, "images from the lane's own elements");
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kXRegWarps + (threadIdx.x >> 5);
+  pdl_begin();
+  if (w >= b.nitems) return;
+  const XItem it = static_cast<const XItem*>(b.items)[w];
+  const SlotDesc& d = b.slots[it.slot];
+  const int nx = d.nx, pitch = d.pitch;
+  const int L = nx / EPL, RP = it.group;     // lanes per row, rows per pass
+  const int rp = lane / L, li = lane - rp * L;
+  const bool lane_on = rp < RP;
+  const bool first = li == 0, last = li == L - 1;
+  const int x0 = EPL * li;
+  const unsigned int row_mask = !lane_on ? 0u : (L >= 32 ? 0xffffffffu : ((1u << L) - 1u) << (rp * L));
+  float wt[W + 1];
+  {
+    const float* wsrc = d.wt[0] + (kBandHalfMax - W);
+#pragma unroll
+    for (int k = 0; k <= W; ++k) wt[k] = wsrc[W + k];
+  }
+  float fx[EPL];
+  {
+    const float4* fxv = reinterpret_cast<const float4*>(static_cast<const float*>(d.fx) + x0);
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+      const float4 f = lane_on ? __ldg(fxv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      fx[4 * q] = f.x;
+      fx[4 * q + 1] = f.y;
+      fx[4 * q + 2] = f.z;
+      fx[4 * q + 3] = f.w;
+    }
+  }
+  const float s = (float)(*d.scale);
+  const float dtg = d.dtg;
+  float* field = static_cast<float*>(d.field);
+  const float* fyz = static_cast<const float*>(d.fyz);
+  const long long nel = (long long)d.ny * d.nz * pitch;
+  const int npass = (it.nrow + RP - 1) / RP;
+  auto row_of = [&](int q) { return it.row0 + (long long)q * RP + rp; };
+  auto valid = [&](int q) { return lane_on && q * RP + rp < it.nrow; };
+  auto load_row = [&](int q, float4 (&buf)[VPL]) {
+    const long long r = row_of(q);
+    const bool ok = valid(q) && GP_IN(r * pitch + x0 + EPL - 1, nel, b.status);
+    const float4* src = reinterpret_cast<const float4*>(field + (size_t)(ok ? r : 0) * pitch + x0);
+#pragma unroll
+    for (int qq = 0; qq < VPL; ++qq) buf[qq] = ok ? src[qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  float4 cur[VPL], nxt[VPL];
+  load_row(0, cur);
+  float fr = valid(0) ? fyz[row_of(0)] : 0.f;
+  for (int q = 0; q < npass; ++q) {
+    float frn = fr;
+    if (q + 1 < npass) {
+      load_row(q + 1, nxt);
+      frn = valid(q + 1) ? fyz[row_of(q + 1)] : 0.f;
+    }
+    float v[EPL];
+#pragma unroll
+    for (int qq = 0; qq < VPL; ++qq) {
+      v[4 * qq] = cur[qq].x * s;
+      v[4 * qq + 1] = cur[qq].y * s;
+      v[4 * qq + 2] = cur[qq].z * s;
+      v[4 * qq + 3] = cur[qq].w * s;
+    }
+    // the same operations in the same order as the copy-fed kernel (x_band_rows), so
+    // that a slot gets the same bits from either
+    float ymax = 0.f;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) ymax = fmaxf(ymax, fabsf(dtg * F::abs2(v[e])));
+    // the row takes the polynomial when every argument of its lanes allows it
+    const unsigned int big = __ballot_sync(0xffffffffu, ymax > 0.0625f || !(ymax == ymax));
+    if ((big & row_mask) == 0u) {
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) v[e] = F::nonlinear_small(v[e], F::mul(fx[e], fr), dtg * F::abs2(v[e]));
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) v[e] = F::nonlinear_full(v[e], F::mul(fx[e], fr), dtg * F::abs2(v[e]));
+    }
+    float lo[W + 1], hi[W + 1];
+#pragma unroll
+    for (int m = 1; m <= W; ++m) {
+      lo[m] = __shfl_up_sync(0xffffffffu, v[EPL - m], 1);
+      hi[m] = __shfl_down_sync(0xffffffffu, v[m - 1], 1);
+      if (first) lo[m] = m == 1 ? 0.f : -v[m - 2];
+      if (last) hi[m] = m == 1 ? 0.f : -v[EPL + 1 - m];
+    }
+    auto win = [&](int j) -> float { return j < 0 ? lo[-j] : (j >= EPL ? hi[j - EPL + 1] : v[j]); };
+    const long long r = row_of(q);
+    const bool store = valid(q) && GP_IN(r * pitch + x0 + EPL - 1, nel, b.status);
+    float4* dst = reinterpret_cast<float4*>(field + (size_t)(store ? r : 0) * pitch + x0);
+#pragma unroll
+    for (int qq = 0; qq < VPL; ++qq) {
+      float o[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = 4 * qq + t;
+        float acc = wt[0] * v[e];
+#pragma unroll
+        for (int k = 1; k <= W; ++k) acc = fmaf(wt[k], win(e - k) + win(e + k), acc);
+        o[t] = v[e] + acc;
+      }
+      if (store) dst[qq] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+#pragma unroll
+    for (int qq = 0; qq < VPL; ++qq) cur[qq] = nxt[qq];
+    fr = frn;
+  }
+}
+
 // y (AXIS 1) or z (AXIS 2) sweep as the banded operator on the odd extension (see the
 // x sweep above), for the FP32 field.  Thread t owns the 16-byte vector
 // xv = t mod nvec (EPT consecutive x) of one segment of band_seg points of one line;
@@ -1797,6 +1920,11 @@ cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_block
 template <int W>
 static cudaError_t launch_batch_W(int axis, const BatchArgs& b, bool cplx, int grid, size_t smem,
                                   cudaStream_t st) {
+  if (axis == 0 && b.x_reg) {
+    if constexpr (W <= 7)
+      if (!cplx) return launch_pdl(k_batch_x_reg<W>, grid, 32 * kXRegWarps, 0, st, b);
+    return cudaErrorInvalidValue;
+  }
   if (axis == 0)
     return cplx ? launch_pdl(k_batch_x_band<float, true, W>, grid, 32 * kBatchXWarps, smem, st, b)
                 : launch_pdl(k_batch_x_band<float, false, W>, grid, 32 * kBatchXWarps, smem, st, b);
@@ -1806,6 +1934,12 @@ static cudaError_t launch_batch_W(int axis, const BatchArgs& b, bool cplx, int g
                 : launch_pdl(k_batch_band_line<float, false, 1, false, W>, grid, 128, ysmem, st, b);
   return cplx ? launch_pdl(k_batch_band_line<float, true, 2, false, W>, grid, 128, ysmem, st, b)
               : launch_pdl(k_batch_band_line<float, false, 2, true, W>, grid, 128, ysmem, st, b);
+}
+
+cudaError_t batch_x_reg_prepare(int w, int* blocks_per_sm) {
+  void (*k)(BatchArgs) = w == 3 ? k_batch_x_reg<3> : w == 5 ? k_batch_x_reg<5> : nullptr;
+  if (!k) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * kXRegWarps, 0);
 }
 
 cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,

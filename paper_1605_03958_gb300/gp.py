@@ -534,7 +534,10 @@ def gp_pool_info(pool) -> dict:
     _pcheck(load_library().gp_pool_info(pool, v), pool)
     keys = ("live", "bytes_used", "x_stages", "seg_turns", "graph", "launches_per_step",
             "free_bytes", "largest_free")
-    return dict(zip(keys, list(v)))
+    d = dict(zip(keys, list(v)))
+    d["x_reg"] = (d["graph"] >> 1) & 1
+    d["graph"] &= 1
+    return d
 
 
 class Pool:

@@ -179,3 +179,24 @@ def test_pool_rejects_and_reports(P):
     assert pool.info()["live"] == 0
     pool.step(3)   # nothing live: a no-op
     pool.close()
+
+
+def test_pool_register_row_x_gives_the_copy_fed_bits(P, monkeypatch):
+    """A pool whose imaginary-time slots all have rows of 16 m points runs the x sweep with
+    rows in registers (16 points per lane, several rows per warp); it gives the same bits
+    as the copy-fed x sweep (same operations in the same order), which a mix with any
+    other row length runs."""
+    slots = [dict(nx=48, ny=32, nz=40, gamma=1.0, nu=1.4, lam=2.2, g=30.0),
+             dict(nx=160, ny=20, nz=18, gamma=0.7, nu=1.9, lam=1.2, g=400.0),
+             dict(nx=32, ny=16, nz=24, gamma=2.5, nu=0.8, lam=1.6, g=5.0)]
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GP_X_REG", flag)
+        pool, ids = make_pool(P, slots)
+        pool.step(12)
+        outs[flag] = ([pool.get_psi(s) for s in ids], pool.info()["x_reg"])
+        pool.close()
+    monkeypatch.delenv("GP_X_REG", raising=False)
+    assert outs["1"][1] == 1 and outs["0"][1] == 0
+    for a, b in zip(outs["1"][0], outs["0"][0]):
+        assert np.array_equal(a, b)
