@@ -39,12 +39,14 @@ class Server:
 
     def __init__(self, arena_bytes: Optional[int] = None, max_slots: int = 1024,
                  quantum: int = 100, tune: bool = False, backfill: bool = True,
-                 max_head_wait_s: float = 1.0):
+                 max_head_wait_s: float = 1.0, graph: Optional[bool] = None):
         if arena_bytes is None:
             import torch
             free, _ = torch.cuda.mem_get_info()
             arena_bytes = int(free * 0.5)
         self.pool = Pool(arena_bytes, max_slots)
+        if graph is not None:
+            self.pool.set_graph(graph)
         self.quantum = int(quantum)
         self.tune = tune
         self.backfill = bool(backfill)
