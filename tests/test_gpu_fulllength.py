@@ -113,14 +113,44 @@ def test_c2_ground_state_fp64_full_length(P, g):
     for a in range(3):
         ref = unpack(fx["density1d"][a])
         assert np.max(np.abs(dens[a] - ref)) <= 1e-11 * np.max(ref), a
-    if g == 0:
-        # the exact discrete fixed point, independent of the oracle
-        nx, ny, nz = fx["grid"]
-        h, (wx, wy, wz), dt = fx["h"], fx["trap"], fx["dt"]
-        want = np.einsum("k,j,i->kji", fixed_point_1d(nz, h, wz, dt), fixed_point_1d(ny, h, wy, dt),
-                         fixed_point_1d(nx, h, wx, dt))
-        want /= np.sqrt(np.sum(want ** 2) * h ** 3)
-        assert np.max(np.abs(psi - want)) <= 1e-10
+
+
+# C2's parameters, for the g = 0 check that needs no oracle fixture
+C2 = {"grid": (240, 200, 160), "h": 0.1, "dt_imag": 0.1 * 0.1 * 0.1, "trap": (1.0, 1.41, 2.0),
+      "steps_imag": 10_000}
+
+
+def exact_fixed_point_g0():
+    """The g = 0 discrete fixed point of C2's step: the step factorises over the axes
+    (pointwise exp(-dt V) is a product of per-axis factors, each CN solve acts on one
+    axis), so its dominant eigenvector is the tensor product of the three 1D ones."""
+    nx, ny, nz = C2["grid"]
+    h, (wx, wy, wz), dt = C2["h"], C2["trap"], C2["dt_imag"]
+    want = np.einsum("k,j,i->kji", fixed_point_1d(nz, h, wz, dt), fixed_point_1d(ny, h, wy, dt),
+                     fixed_point_1d(nx, h, wx, dt))
+    return want / np.sqrt(np.sum(want ** 2) * h ** 3)
+
+
+def test_c2_g0_exact_fixed_point_fp64(P):
+    """10^4 FP64 steps at g = 0 against the exact discrete fixed point (no oracle
+    involved).  The start is the trap's continuum Gaussian: its overlap with the first
+    even excited state (2 trap quanta above along x) is O(h^2) and decays by
+    exp(-2 dt 10^4) = exp(-20) = 2e-9, which leaves a remainder near 1e-11."""
+    s = ground_state(P, C2, 0.0, "f64")
+    psi = s.get_psi()
+    s.close()
+    assert np.max(np.abs(psi - exact_fixed_point_g0())) <= 1e-10
+
+
+def test_c2_g0_exact_fixed_point_fp32(P):
+    """The same with the FP32 field, at the FP32 ground-state tolerances (relative L2
+    of the density <= 1e-5)."""
+    s = ground_state(P, C2, 0.0, "f32")
+    psi = s.get_psi()
+    s.close()
+    want = exact_fixed_point_g0()
+    d_got, d_ref = psi.astype(np.float64) ** 2, want ** 2
+    assert np.sqrt(np.sum((d_got - d_ref) ** 2) / np.sum(d_ref ** 2)) <= 1e-5
 
 
 @pytest.mark.parametrize("g", [0, 100, 2000])
