@@ -430,22 +430,37 @@ def batch_short(P, args):
             "mu_rel_vs_f64_max": max(err), "accuracy_instances": len(err)}
 
 
+def serve_summary(done):
+    """solves / s over the run (first arrival to last finish), latency percentiles, the
+    offered rate and the p99 latency by quarter of the request index (flat quarters: the
+    server keeps up; growing ones: the queue grows)."""
+    import numpy as np
+    lat = sorted(d["latency"] for d in done)
+    span = max(d["finished"] for d in done) - min(d["arrival"] for d in done)
+    arr = sorted(d["arrival"] for d in done)
+    out = {"solves": len(done), "solves_per_s": round(len(done) / span, 3),
+           "p50_s": round(float(np.percentile(lat, 50)), 4),
+           "p99_s": round(float(np.percentile(lat, 99)), 4), "makespan_s": round(span, 3)}
+    if len(done) >= 8 and arr[-1] > arr[0]:
+        out["offered_per_s"] = round((len(arr) - 1) / (arr[-1] - arr[0]), 3)
+        by_id = [d["latency"] for d in sorted(done, key=lambda d: d["id"])]
+        q = len(by_id) // 4
+        out["p99_by_quarter_s"] = [round(float(np.percentile(by_id[i * q:(i + 1) * q if i < 3 else None], 99)), 4)
+                                   for i in range(4)]
+    return out
+
+
 def serve_short(P, args):
-    """A shortened serving run: the first 300 requests of the seeded stream (Poisson at
-    200 / s) through the continuous-batching server, and the leading 50 one at a time
-    with FP64 single solvers (arrivals on the wall clock in both)."""
+    """The serving workload in the default line's context: the seeded request stream
+    (--serve-requests, Poisson at 200 / s) through the continuous-batching server, and
+    the leading 50 requests one at a time with FP64 single solvers (arrivals on the wall
+    clock in both)."""
     import numpy as np
     from paper_1605_03958_gb300 import workloads
     from paper_1605_03958_gb300.serve import Server, serve_one_at_a_time
 
-    def summary(done):
-        lat = sorted(d["latency"] for d in done)
-        span = max(d["finished"] for d in done) - min(d["arrival"] for d in done)
-        return {"solves": len(done), "solves_per_s": round(len(done) / span, 3),
-                "p50_s": round(float(np.percentile(lat, 50)), 4),
-                "p99_s": round(float(np.percentile(lat, 99)), 4)}
-
-    reqs = workloads.serve_requests(300)
+    summary = serve_summary
+    reqs = workloads.serve_requests(args.serve_requests)
     srv = Server(quantum=100)
     done = srv.run(reqs, realtime=True)
     srv.close()
@@ -461,7 +476,7 @@ def serve_short(P, args):
             gerr = max(gerr, abs(d["obs"]["mu"] - w["mu"]) / abs(w["mu"]))
         else:
             qerr = max(qerr, abs(d["obs"]["energy"] - w["energy"]) / abs(w["energy"]))
-    return {"workload": "first 300 requests, Poisson arrivals at 200/s (seed 3958): 70 % ground "
+    return {"workload": f"{len(reqs)} requests, Poisson arrivals at 200/s (seed 3958): 70 % ground "
                         "state (2000 imaginary steps), 30 % quench (500..5000 real steps)",
             "batched": summary(done),
             "one_at_a_time_f64_first_50": summary(f64),
@@ -917,12 +932,7 @@ def run_serve(args):
     from paper_1605_03958_gb300 import workloads
     from paper_1605_03958_gb300.serve import Server, serve_one_at_a_time
 
-    def summary(done):
-        lat = sorted(d["latency"] for d in done)
-        span = max(d["finished"] for d in done) - min(d["arrival"] for d in done)
-        return {"solves": len(done), "solves_per_s": round(len(done) / span, 3),
-                "p50_s": round(float(np.percentile(lat, 50)), 4),
-                "p99_s": round(float(np.percentile(lat, 99)), 4), "makespan_s": round(span, 3)}
+    summary = serve_summary
 
     import numpy as np
     reqs = workloads.serve_requests(args.serve_requests)
@@ -934,20 +944,25 @@ def run_serve(args):
     srv.close()
 
     head = reqs[:args.serve_compare]
-    srv = Server(quantum=100)
-    b = srv.run(head, realtime=True)
-    srv.close()
-    f64 = serve_one_at_a_time(head, prec="f64", realtime=True)
-    f32 = serve_one_at_a_time(head, prec="f32", realtime=True)
-    by = {d["id"]: d for d in f64}
-    err = {"ground_mu_rel_max": 0.0, "quench_energy_rel_max": 0.0}
-    for d in b:
-        w = by[d["id"]]["obs"]
-        if d["kind"] == "ground":
-            err["ground_mu_rel_max"] = max(err["ground_mu_rel_max"], abs(d["obs"]["mu"] - w["mu"]) / abs(w["mu"]))
-        else:
-            err["quench_energy_rel_max"] = max(err["quench_energy_rel_max"],
-                                               abs(d["obs"]["energy"] - w["energy"]) / abs(w["energy"]))
+    compare = None
+    if head:
+        srv = Server(quantum=100)
+        b = srv.run(head, realtime=True)
+        srv.close()
+        f64 = serve_one_at_a_time(head, prec="f64", realtime=True)
+        f32 = serve_one_at_a_time(head, prec="f32", realtime=True)
+        by = {d["id"]: d for d in f64}
+        err = {"ground_mu_rel_max": 0.0, "quench_energy_rel_max": 0.0}
+        for d in b:
+            w = by[d["id"]]["obs"]
+            if d["kind"] == "ground":
+                err["ground_mu_rel_max"] = max(err["ground_mu_rel_max"],
+                                               abs(d["obs"]["mu"] - w["mu"]) / abs(w["mu"]))
+            else:
+                err["quench_energy_rel_max"] = max(err["quench_energy_rel_max"],
+                                                   abs(d["obs"]["energy"] - w["energy"]) / abs(w["energy"]))
+        compare = {"requests": len(head), "batched": summary(b), "one_at_a_time_f64": summary(f64),
+                   "one_at_a_time_f32": summary(f32), "accuracy_vs_f64": err}
     line = {
         "metric": "served solves/s", "value": full["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
         "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -956,12 +971,12 @@ def run_serve(args):
                                "ground state (2000 imaginary steps), 30 % quench (500..5000 real "
                                "steps from the g=0 Gaussian); extents multiples of 16 in "
                                "[32,128]x[32,96]x[32,64], g log-uniform [1,1000], h=0.2, dt=0.1h^2",
-                   "quantum_steps": 100, "admission": "FIFO by free arena (half of free HBM)"},
+                   "quantum_steps": 100,
+                   "admission": "arrival order with backfill past a request that does not fit "
+                                "(head wait bound 1 s); arena = half of free HBM"},
         "latency": {"p50_s": full["p50_s"], "p99_s": full["p99_s"]},
         "run": full, "server": stats,
-        "compare_first_requests": {"requests": len(head), "batched": summary(b),
-                                   "one_at_a_time_f64": summary(f64), "one_at_a_time_f32": summary(f32),
-                                   "accuracy_vs_f64": err},
+        "compare_first_requests": compare,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

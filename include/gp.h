@@ -144,9 +144,10 @@ int gp_get_psi(gp_solver* s, double* host, int as_complex);
  * float host buffers (nx*ny*nz floats, or 2*nx*ny*nz interleaved), one contiguous
  * host copy each way with no FP64 conversion (rows are re-pitched on the device when
  * the field's row pitch exceeds nx).
- * gp_get_psi_f32 folds the pending renormalisation factor into the field first (the
- * field is then stored normalised; nothing else changes).  as_complex must match the
- * field (0: real, 1: complex), else GP_ERR_STATE; FP64 solvers return GP_ERR_ARG.
+ * gp_get_psi_f32 returns the field times the pending renormalisation factor (packed
+ * on the device in the solver's staging area; the solver's state is left as it is, so
+ * a read does not change the bits of later steps).  as_complex must match the field
+ * (0: real, 1: complex), else GP_ERR_STATE; FP64 solvers return GP_ERR_ARG.
  * gp_get_psi_f32 synchronises.                                                      */
 int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex);
 int gp_get_psi_f32(gp_solver* s, float* host, int as_complex);
@@ -365,8 +366,9 @@ int gp_pool_set_graph(gp_pool* pool, int enable);
 
 /* info[0] live slots, [1] arena bytes in use, [2] x_stages, [3] seg_turns,
  * [4] bit 0: a step graph is instantiated, bit 1: the imaginary-time slots' x sweep
- * holds each row in registers (every such slot has rows of 16 m <= 512 points), [5]
- * launches per step, [6] free arena bytes, [7] largest free range.                */
+ * holds each row in registers (every such slot has rows of 16 m <= 512 points), bit 2:
+ * the real-time slots' x sweep does (every such slot has rows of 8 m <= 256 complex
+ * points), [5] launches per step, [6] free arena bytes, [7] largest free range.     */
 int gp_pool_info(const gp_pool* pool, long long info[8]);
 const char* gp_pool_last_error(const gp_pool* pool);
 

@@ -319,6 +319,8 @@ struct gp_solver {
   bool line64 = false;               // FP64 field: the line-streaming sweeps of gp_sweeps64.cu
   bool defer_norm = false;           // FP32 real field: the z sweep's norm finished by its reader
   int* scale_state = nullptr;        // device: 1 while the factor is in the z sweep's partials
+  unsigned int* step_ctr = nullptr;  // device: imaginary-time steps since the field was set
+                                     // (the FP32 factor's dither, step_dither)
   int split = GP_SPLIT_LIE;          // splitting of a step
   bool kinetic_only = false;         // x sweep without the pointwise substep (Strang)
   float band_wt[2][3][2 * 17] = {};  // its weights (complex: pairs)
@@ -458,6 +460,8 @@ void fill_sweep_params(gp_solver* s) {
       q.band_dtg = (float)(p.dt * s->g);
       q.pw = 1;
       q.scale = s->scale;
+      // FP32 field in imaginary time: the renormalisation factor is dithered per step
+      q.step_ctr = (m == 0 && s->L.rbytes == 4) ? s->step_ctr : nullptr;
       q.partials = s->partials;
       q.counter = s->counters;
       q.scale_out = s->scale;
@@ -522,9 +526,9 @@ void fill_sweep_params(gp_solver* s) {
             bps > 0) {
           // rows per warp such that every warp is resident at once with equal work
           const long long rows = (long long)p.ny * p.nz;
-          const long long cap = (long long)s->nsm * bps * gpk::kBandWarps;
-          q.band_rows = (int)((rows + cap - 1) / cap);
-          const long long warps = (rows + q.band_rows - 1) / q.band_rows;
+          const long long warps = std::min((long long)s->nsm * bps * gpk::kBandWarps, rows);
+          q.band_rows = (int)(rows / warps);
+          q.band_rem = (int)(rows % warps);
           s->fast_grid[m][0] = (int)((warps + gpk::kBandWarps - 1) / gpk::kBandWarps);
         } else {
           cudaGetLastError();
@@ -537,9 +541,9 @@ void fill_sweep_params(gp_solver* s) {
         if (q.band_w && m == 0 && gpk::x_reg_fits(p.nx, q.band_w) && x_reg_enabled() &&
             gpk::x_reg_prepare(q.band_w, m == 1, &rbps) == cudaSuccess && rbps > 0) {
           const long long rows = (long long)p.ny * p.nz;
-          const long long cap = (long long)s->nsm * rbps * gpk::kXRegWarps;
-          q.band_rows = (int)((rows + cap - 1) / cap);
-          const long long warps = (rows + q.band_rows - 1) / q.band_rows;
+          const long long warps = std::min((long long)s->nsm * rbps * gpk::kXRegWarps, rows);
+          q.band_rows = (int)(rows / warps);
+          q.band_rem = (int)(rows % warps);
           s->fast_grid[m][0] = (int)((warps + gpk::kXRegWarps - 1) / gpk::kXRegWarps);
           q.band_reg = 1;
         }
@@ -749,6 +753,13 @@ int set_scale_one(gp_solver* s) {
   return GP_OK;
 }
 
+// A new field: its imaginary-time steps (the FP32 factor's dither) count from zero, so
+// that the same field and the same steps give the same bits in any solver.
+int reset_steps(gp_solver* s) {
+  GP_CUDA(s, cudaMemsetAsync(s->step_ctr, 0, sizeof(unsigned int), s->stream));
+  return GP_OK;
+}
+
 int create_impl(const gp_params* p, void* dev_buf, size_t bytes, void* stream, gp_solver** out) {
   if (!out) {
     g_create_error = "out is NULL";
@@ -804,6 +815,7 @@ int create_impl(const gp_params* p, void* dev_buf, size_t bytes, void* stream, g
   s->obs = reinterpret_cast<double*>(sc + 64);
   s->status = reinterpret_cast<int*>(sc + 256);
   s->scale_state = reinterpret_cast<int*>(sc + 160);
+  s->step_ctr = reinterpret_cast<unsigned int*>(sc + 192);
   s->counters = reinterpret_cast<unsigned int*>(sc + 320);
 
   int rc = GP_OK;
@@ -1204,7 +1216,7 @@ int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
   e = is_f64(s) ? gpk::launch_norm_to_scale<double>(f, s->stream)
                 : gpk::launch_norm_to_scale<float>(f, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "norm");
-  return GP_OK;
+  return reset_steps(s);
 }
 
 int gp_set_psi(gp_solver* s, const double* host, int is_complex) {
@@ -1217,7 +1229,8 @@ int gp_set_psi(gp_solver* s, const double* host, int is_complex) {
   cudaError_t e = is_f64(s) ? gpk::launch_import<double>(f, s->staging, s->is_complex, s->stream)
                             : gpk::launch_import<float>(f, s->staging, s->is_complex, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "import");
-  return set_scale_one(s);
+  const int rc = set_scale_one(s);
+  return rc != GP_OK ? rc : reset_steps(s);
 }
 
 int gp_get_psi(gp_solver* s, double* host, int as_complex) {
@@ -1252,7 +1265,8 @@ int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex) {
     GP_CUDA(s, cudaMemset2DAsync(static_cast<unsigned char*>(s->field) + row, pitch, 0, pitch - row, rows,
                                  s->stream));   // pad columns stay zero
   }
-  return set_scale_one(s);
+  const int rc = set_scale_one(s);
+  return rc != GP_OK ? rc : reset_steps(s);
 }
 
 int gp_get_psi_f32(gp_solver* s, float* host, int as_complex) {
@@ -1262,22 +1276,13 @@ int gp_get_psi_f32(gp_solver* s, float* host, int as_complex) {
     return fail(s, GP_ERR_STATE, "as_complex must match the field (0: real, 1: complex)");
   wait_copies(s);
   const int m = as_complex;
-  if (!s->is_complex) {   // fold the pending renormalisation factor into the field
-    const FieldParams f = field_params(s);
-    const cudaError_t e = gpk::launch_fold_scale<float>(f, false, s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "fold");
-    const int rc = set_scale_one(s);
-    if (rc != GP_OK) return rc;
-  }
-  const size_t eb = (size_t)4 * (m + 1), pitch = (size_t)s->L.pitch[m] * eb, row = (size_t)s->prm.nx * eb;
-  const size_t rows = (size_t)s->prm.ny * s->prm.nz;
-  if (pitch == row) {
-    GP_CUDA(s, cudaMemcpyAsync(host, s->field, rows * row, cudaMemcpyDeviceToHost, s->stream));
-  } else {
-    GP_CUDA(s, cudaMemcpy2DAsync(s->staging, row, s->field, pitch, row, rows, cudaMemcpyDeviceToDevice,
-                                 s->stream));
-    GP_CUDA(s, cudaMemcpyAsync(host, s->staging, rows * row, cudaMemcpyDeviceToHost, s->stream));
-  }
+  // the field times the pending factor, packed into the staging area (the field and
+  // its factor stay as they are: a read does not change the next steps' bits)
+  const size_t bytes = (size_t)4 * (m + 1) * s->prm.nx * s->prm.ny * s->prm.nz;
+  float* packed = reinterpret_cast<float*>(s->staging);
+  const cudaError_t e = gpk::launch_export_f32(field_params(s), m == 1, packed, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "export");
+  GP_CUDA(s, cudaMemcpyAsync(host, packed, bytes, cudaMemcpyDeviceToHost, s->stream));
   return check_status(s);
 }
 

@@ -328,14 +328,16 @@ int rebuild(gp_pool* P) {
     }
     // x: stages that fit shared memory, rows per group per slot, rows per warp such
     // that every warp is resident at once
-    // real slots whose rows are 16 m <= 512 points at a half-width of 3 or 5: rows in
-    // registers, floor(32 / (nx / 16)) rows of a slot per warp pass
-    bool reg = !cplx && (P->wl[m][0] == 3 || P->wl[m][0] == 5) && batch_x_reg_enabled();
+    // slots whose rows are EPL m <= 32 EPL points (EPL = 16 real, 8 complex elements)
+    // at a half-width of 3 or 5: rows in registers, floor(32 / (nx / EPL)) rows of a
+    // slot per warp pass
+    const int epl = cplx ? 8 : 16;
+    bool reg = batch_x_reg_enabled();
     for (int i = 0; i < ns && reg; ++i)
       if (P->slots[i].live && P->slots[i].mode == m)
-        reg = P->slots[i].prm.nx % 16 == 0 && P->slots[i].prm.nx <= 512;
+        reg = gpk::batch_x_reg_fits(P->slots[i].prm.nx, P->wl[m][0], cplx);
     int rbps = 0;
-    if (reg && (gpk::batch_x_reg_prepare(P->wl[m][0], &rbps) != cudaSuccess || rbps <= 0)) {
+    if (reg && (gpk::batch_x_reg_prepare(P->wl[m][0], cplx, &rbps) != cudaSuccess || rbps <= 0)) {
       cudaGetLastError();
       reg = false;
     }
@@ -375,7 +377,7 @@ int rebuild(gp_pool* P) {
       if (!S.live || S.mode != m) continue;
       const long long rows = (long long)S.prm.ny * S.prm.nz;
       // register rows: items of a whole number of passes of rp rows each
-      const int rp = reg ? std::max(1, 32 / (S.prm.nx / 16)) : 1;
+      const int rp = reg ? std::max(1, 32 / (S.prm.nx / epl)) : 1;
       const int ipw = reg ? (rpw + rp - 1) / rp * rp : rpw;
       for (long long r = 0; r < rows; r += ipw) {
         XItem it;
@@ -821,7 +823,7 @@ int gp_pool_info(const gp_pool* P, long long info[8]) {
   info[1] = (long long)(P->capacity - P->alloc.free_total());
   info[2] = P->x_stages;
   info[3] = P->seg_turns;
-  info[4] = (P->exec ? 1 : 0) | (P->x_reg[0] ? 2 : 0);
+  info[4] = (P->exec ? 1 : 0) | (P->x_reg[0] ? 2 : 0) | (P->x_reg[1] ? 4 : 0);
   info[5] = P->launches_per_step;
   info[6] = (long long)P->alloc.free_total();
   info[7] = (long long)P->alloc.largest();

@@ -408,6 +408,20 @@ template <class C> __device__ __forceinline__ C cmul(C a, C b) {
 
 // ----------------------------------------------------------- field policies
 
+// Dither of the renormalisation factor of an FP32 field in imaginary time: step n
+// applies s (1 + xi_n 2^-20), xi_n = (int)(n 0x9E3779B9) / 2^31 in [-1, 1) (a Weyl
+// sequence of the golden ratio, equidistributed).  At the ground state the FP32 field
+// barely changes from step to step, so without it every step would round the same
+// values the same way: a fixed error vector, which imaginary time amplifies by
+// 1 / (dt gap) (about 500 at dt = 0.001).  A factor that moves the values by a few
+// ulps per step turns that into zero-mean noise, which the step damps; the uniform
+// factor itself is removed by the next renormalisation.  ctr = null: no dither.
+__device__ __forceinline__ double step_dither(const unsigned int* ctr) {
+  if (!ctr) return 1.0;
+  const unsigned int u = *ctr * 0x9E3779B9u;
+  return 1.0 + (double)(int)u * 0x1p-51;
+}
+
 template <class R, bool CPLX> struct Field;
 
 // Real field, imaginary time.

@@ -85,7 +85,8 @@ struct SweepParams {
   const void* band_fyz;  // trap factor per row r = k ny + j: exp(-dt (V_y + V_z)) or cis(..)
   float band_wt[2 * 17]; // free-line CN row w_{k - band_w}, k = 0 .. 2 band_w, centre as w_0 - 1 (complex: pairs)
   int band_w;            // half-width W of the band (3, 5 or 8)
-  int band_rows;         // x: consecutive rows per warp
+  int band_rows;         // x: consecutive rows per warp; the first band_rem warps take one more
+  int band_rem;
   int band_stages;       // x: groups of rows in flight per warp
   int band_group;        // x: rows per group (worked on together by the warp's lanes)
   int band_seg;          // y / z: points per line segment (a multiple of 2 band_w + 1)
@@ -112,6 +113,10 @@ struct SweepParams {
   int norm_copies;       // z stores norm_copies copies of its partials (copy c at c norm_blocks);
                          // x block b reads copy b mod norm_copies: fewer readers per L2 line
   int* scale_state;      // 1: the factor is the partials' 1 / sqrt(sum dV)
+  // FP32 field in imaginary time: the step counter behind the renormalisation factor's
+  // dither (step_dither in gp_device.cuh): the sweeps that apply the factor read it, the
+  // y sweep adds one; null otherwise (no dither)
+  unsigned int* step_ctr;
   int* status;
   double dV;
   long long ntiles;
@@ -214,9 +219,11 @@ int x_band_group(int nx, int ept, int stages, size_t slot_bytes, size_t warp_bud
 cudaError_t batch_prepare(int w, bool complex_field, size_t x_smem, int* x_blocks_per_sm);
 cudaError_t launch_batch_sweep(int axis, int w, const BatchArgs& b, bool complex_field, int grid,
                                size_t smem, cudaStream_t st);
-// Batched x sweep with rows in registers (real slots of nx = 16 m <= 512, W in {3, 5}):
-// resident blocks of kXRegWarps warps per SM.
-cudaError_t batch_x_reg_prepare(int w, int* blocks_per_sm);
+// Batched x sweep with rows in registers (slots of nx = 16 m <= 512 real or 8 m <= 256
+// complex points, W in {3, 5}): whether a slot fits, and the resident blocks of
+// kXRegWarps warps per SM.
+bool batch_x_reg_fits(int nx, int w, bool complex_field);
+cudaError_t batch_x_reg_prepare(int w, bool complex_field, int* blocks_per_sm);
 // FP64 sweeps (gp_sweeps64.cu): x moves 32 rows per warp through shared-memory
 // chunks (dynamic shared memory x64_smem), y / z stream one line per thread; the
 // launch covers the whole grid (sweep64_blocks blocks).  sweep64_prepare sets the x
@@ -242,9 +249,6 @@ template <class R> cudaError_t launch_norm_to_scale(const FieldParams& p, cudaSt
 // *scale (non-finite or zero norm flagged in *status), and *state = 0 (one block).
 cudaError_t launch_resolve_scale(double* scale, int* state, const double* partials, int nb,
                                  double dV, int* status, cudaStream_t st);
-// psi <- *p.scale psi in place (the caller then sets the factor to 1).
-template <class R> cudaError_t launch_fold_scale(const FieldParams& p, bool complex_field,
-                                                 cudaStream_t st);
 // FP32 field times *p.scale, packed into rows of nx elements in dst (not aliasing the
 // field); the field and the factor are left as they are.
 cudaError_t launch_export_f32(const FieldParams& p, bool complex_field, float* dst, cudaStream_t st);

@@ -236,22 +236,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_half_pointwise(const FieldPa
   }
 }
 
-// ------------------------------------------------- fold the pending factor
-
-template <class R, bool CPLX>
-__global__ void k_fold_scale(const FieldParams p) {
-  using F = Field<R, CPLX>;
-  using E = typename F::E;
-  const R s = (R)(*p.scale);
-  E* psi = static_cast<E*>(p.psi);
-  const long long nrows = (long long)p.ny * p.nz;
-  for (long long r = blockIdx.x; r < nrows; r += gridDim.x)
-    for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
-      const size_t idx = (size_t)r * p.pitch + i;
-      psi[idx] = F::scaled(psi[idx], s);
-    }
-}
-
 // FP32 field (words = 1 real, 2 complex floats per element) times the pending factor,
 // packed into rows of nx elements in dst (not the field): 16-byte vectors when the
 // rows are contiguous and a multiple of four floats, else one float per thread.
@@ -452,12 +436,6 @@ cudaError_t launch_half_pointwise(const FieldParams& p, bool complex_field, cons
   return cudaGetLastError();
 }
 
-template <class R>
-cudaError_t launch_fold_scale(const FieldParams& p, bool complex_field, cudaStream_t st) {
-  if (complex_field) k_fold_scale<R, true><<<grid_for_rows(p), 256, 0, st>>>(p);
-  else k_fold_scale<R, false><<<grid_for_rows(p), 256, 0, st>>>(p);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_export_f32(const FieldParams& p, bool complex_field, float* dst, cudaStream_t st) {
   k_export_f32<<<grid_for_rows(p), 256, 0, st>>>(p, complex_field ? 2 : 1, dst);
@@ -527,7 +505,6 @@ cudaError_t launch_cols_sum(const double* in, int rows, int cols, double w, doub
   template cudaError_t launch_norm_to_scale<R>(const FieldParams&, cudaStream_t);             \
   template cudaError_t launch_half_pointwise<R>(const FieldParams&, bool, const void*,       \
                                                 const void*, double, bool, bool, cudaStream_t); \
-  template cudaError_t launch_fold_scale<R>(const FieldParams&, bool, cudaStream_t);        \
   template cudaError_t launch_init_gaussian<R>(const FieldParams&, double, double, double,    \
                                                cudaStream_t);                                  \
   template cudaError_t launch_import<R>(const FieldParams&, const double*, bool, cudaStream_t); \

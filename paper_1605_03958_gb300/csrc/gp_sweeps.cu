@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
     const int k = (int)(r / p.ny);
     const E* fxt = static_cast<const E*>(p.band_fx);                      // trap factor along x
     const E fr = __ldg(static_cast<const E*>(p.band_fyz) + (size_t)k * p.ny + j);   // of this row
-    const R s = (R)(*p.scale);
+    const R s = (R)(*p.scale * step_dither(p.step_ctr));
     const R dtg = (R)(p.dt * p.g);
     const E* A = static_cast<const E*>(p.A);
     const E* B = static_cast<const E*>(p.B);
@@ -240,6 +240,8 @@ template <class R, bool CPLX>
 __global__ void __launch_bounds__(32) k_sweep_y(const __grid_constant__ CUtensorMap map,
                                                 const SweepParams p) {
   pdl_begin();
+  // the factor's dither (FP32, imaginary time): the step's x sweep has read the counter
+  if (p.step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *p.step_ctr += 1;
   using E = typename Field<R, CPLX>::E;
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x;
@@ -385,6 +387,8 @@ __device__ __forceinline__ void norm_block_finish(double acc, const SweepParams&
 template <class R, bool CPLX, int AXIS, bool NORM, int L>
 __global__ void __launch_bounds__(128, CPLX ? 4 : GP_STREAM_MINB) k_sweep_stream(const SweepParams p) {
   pdl_begin();
+  // the factor's dither (FP32, imaginary time): the step's x sweep has read the counter
+  if (AXIS == 1 && p.step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *p.step_ctr += 1;
   using F = Field<R, CPLX>;
   using E = typename F::E;
   constexpr int U = kStreamU;
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
   const E* B = static_cast<const E*>(p.B);
   const E Ab = __ldg(A + nx - 1), Bb = __ldg(B + nx - 1);
   const R* vx = static_cast<const R*>(p.vx);
-  const R s = (R)(*p.scale);
+  const R s = (R)(*p.scale * step_dither(p.step_ctr));
   const R dt = (R)p.dt, g = (R)p.g;
   const long long myrow = r0 + min(lane, rows - 1);
   const int jrow = (int)(myrow % p.ny), krow = (int)(myrow / p.ny);
@@ -701,6 +705,7 @@ template <class E> struct XRows {
   const E* fyz;          // trap factor per row
   const E* wt;           // w_{k-W}, k = 0 .. 2W (centre as w_0 - 1)
   const double* scale;   // pending renormalisation factor
+  double dither;         // its step dither (step_dither; 1 for none)
   int* status;
   unsigned long long wait_ns;   // limit of the first bounded wait on each row copy
   long long row0;
@@ -742,7 +747,7 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
   const float4* fx = a.fx;
   const E* fyz = a.fyz;
   const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
-  const R s = (R)(*a.scale);
+  const R s = (R)(*a.scale * a.dither);
   const R dtg = (R)a.dtg;
   // row slot r of stage st
   auto slot_of = [&](int st, int r) { return slots + (size_t)(st * G + r) * se; };
@@ -898,7 +903,7 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
 #pragma unroll
   for (int c = 0; c < NC; ++c)
     fxc[c] = lane + 32 * c < nvec ? __ldg(fx + lane + 32 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
-  const R s = (R)(*a.scale);
+  const R s = (R)(*a.scale * a.dither);
   const R dtg = (R)a.dtg;
   const bool pw = a.pw != 0;
   const E* fyz = a.fyz + a.row0;
@@ -1019,8 +1024,10 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   uint64_t* full = reinterpret_cast<uint64_t*>(smem) + wib * S;
   E* slots = reinterpret_cast<E*>(smem + 128 * kBandWarps) + (size_t)wib * S * G * slot_elems + kBandPad;
   const long long nrows = (long long)p.ny * p.nz;
-  const long long row0 = ((long long)blockIdx.x * kBandWarps + wib) * p.band_rows;
-  const int nrow = (int)max(0LL, min((long long)p.band_rows, nrows - row0));
+  // rows in equal shares (band_rows or band_rows + 1 per warp): every SM the same work
+  const int w = blockIdx.x * kBandWarps + wib;
+  const long long row0 = (long long)w * p.band_rows + min(w, p.band_rem);
+  const int nrow = (int)max(0LL, min((long long)p.band_rows + (w < p.band_rem ? 1 : 0), nrows - row0));
   x_band_init(full, slots, S, S * G, slot_elems);
   pdl_begin();
   // the pending factor (see k_sweep_x_reg), for every warp of the block
@@ -1039,6 +1046,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.fyz = static_cast<const E*>(p.band_fyz);
   a.wt = reinterpret_cast<const E*>(p.band_wt);
   a.scale = defer ? &s_factor : p.scale;
+  a.dither = step_dither(p.step_ctr);
   a.status = p.status;
   a.wait_ns = p.wait_ns;
   a.row0 = row0;
@@ -1074,8 +1082,10 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_co
   static_assert(W <= 7, "images from the lane's own eight elements");
   const int lane = threadIdx.x & 31;
   const long long nrows = (long long)p.ny * p.nz;
-  const long long row0 = ((long long)blockIdx.x * kXRegWarps + (threadIdx.x >> 5)) * p.band_rows;
-  const int nrow = (int)max(0LL, min((long long)p.band_rows, nrows - row0));
+  // rows in equal shares (band_rows or band_rows + 1 per warp): every SM the same work
+  const int w = blockIdx.x * kXRegWarps + (threadIdx.x >> 5);
+  const long long row0 = (long long)w * p.band_rows + min(w, p.band_rem);
+  const int nrow = (int)max(0LL, min((long long)p.band_rows + (w < p.band_rem ? 1 : 0), nrows - row0));
   const int nx = p.nx, pitch = p.pitch;
   const int x0 = 8 * lane;
   const bool act = x0 < nx;                  // lanes past the row hold zeros
@@ -1169,10 +1179,11 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_co
     load_row(row0, cur);
     fr = fyz[row0];
   }
-  s = (float)(p.norm_defer
-                   ? deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks,
-                                    p.norm_blocks, p.dV, p.status, blockIdx.x == 0, p.scale_state, p.scale)
-                   : *p.scale);
+  s = (float)((p.norm_defer
+                    ? deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks,
+                                     p.norm_blocks, p.dV, p.status, blockIdx.x == 0, p.scale_state, p.scale)
+                    : *p.scale) *
+              step_dither(p.step_ctr));
   if (nrow == 0) return;
   for (int i = 0; i < nrow; ++i) {
     const long long r = row0 + i;
@@ -1211,6 +1222,7 @@ __global__ void __launch_bounds__(32 * kBatchXWarps) k_batch_x_band(const __grid
   a.fyz = static_cast<const E*>(d.fyz);
   a.wt = reinterpret_cast<const E*>(d.wt[0]) + (kBandHalfMax - W);
   a.scale = d.scale;
+  a.dither = 1.0;
   a.status = b.status;
   a.wait_ns = b.wait_ns;
   a.row0 = it.row0;
@@ -1225,20 +1237,23 @@ __global__ void __launch_bounds__(32 * kBatchXWarps) k_batch_x_band(const __grid
   x_band_rows<R, CPLX, W>(a, full, slots);
 }
 
-// Batched x sweep with rows in registers, for real fields whose every live slot has
-// rows of nx = 16 m <= 512 points (half-width W <= 7): lane li of a row owns its
-// sixteen elements [16 li, 16 li + 16) (four 16-byte vectors).  Warp w takes work item
-// w, it.nrow consecutive rows of one slot, it.group = floor(32 / L) rows at a time
-// (L = nx / 16 lanes per row; rows of 32-160 points fill 27-32 lanes); the next pass's
-// rows in flight while a pass is processed.  Per row as in k_sweep_x_reg: pending
-// factor and pointwise substep in registers, the W neighbours by shuffles from lanes
-// li -/+ 1, odd images at the row's own first and last lanes; the pointwise polynomial
-// is chosen per row (a ballot over the row's lanes), so a slot's arithmetic does not
-// depend on which rows share a warp.
-template <int W>
+// Batched x sweep with rows in registers, for slots whose rows are nx = EPL m points,
+// at most 32 EPL (half-width W <= 7): EPL = 16 real or 8 complex elements per lane, four
+// 16-byte vectors.  Lane li of a row owns its elements [EPL li, EPL li + EPL).  Warp w
+// takes work item w, it.nrow consecutive rows of one slot, it.group = floor(32 / L)
+// rows at a time (L = nx / EPL lanes per row); the next pass's rows are in flight while
+// a pass is processed.  Per row as in k_sweep_x_reg: pending factor and pointwise
+// substep in registers, the W neighbours by shuffles from lanes li -/+ 1, odd images at
+// the row's own first and last lanes.  The pointwise polynomial is chosen per row (a
+// ballot over the row's lanes), so a slot's arithmetic does not depend on which rows
+// share a warp, and the operations are those of the copy-fed kernel (x_band_rows) in
+// the same order.
+template <bool CPLX, int W>
 __global__ void __launch_bounds__(32 * kXRegWarps) k_batch_x_reg(const __grid_constant__ BatchArgs b) {
-  using F = Field<float, false>;
-  constexpr int EPL = 16, VPL = 4;
+  using F = Field<float, CPLX>;
+  using E = typename F::E;
+  constexpr int EPT = 16 / (int)sizeof(E);   // elements per 16-byte vector
+  constexpr int VPL = 4, EPL = VPL * EPT;    // vectors and elements per lane
   static_assert(W <= 7, "images from the lane's own elements");
   const int lane = threadIdx.x & 31;
   const int w = blockIdx.x * kXRegWarps + (threadIdx.x >> 5);
@@ -1253,28 +1268,26 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_batch_x_reg(const __grid_co
   const bool first = li == 0, last = li == L - 1;
   const int x0 = EPL * li;
   const unsigned int row_mask = !lane_on ? 0u : (L >= 32 ? 0xffffffffu : ((1u << L) - 1u) << (rp * L));
-  float wt[W + 1];
+  E wt[W + 1];   // wt[0] = w_0 - 1, wt[k] = w_k
   {
-    const float* wsrc = d.wt[0] + (kBandHalfMax - W);
+    const E* wsrc = reinterpret_cast<const E*>(d.wt[0]) + (kBandHalfMax - W);
 #pragma unroll
     for (int k = 0; k <= W; ++k) wt[k] = wsrc[W + k];
   }
-  float fx[EPL];
+  E fx[EPL];
   {
-    const float4* fxv = reinterpret_cast<const float4*>(static_cast<const float*>(d.fx) + x0);
+    const float4* fxv = reinterpret_cast<const float4*>(static_cast<const E*>(d.fx) + x0);
 #pragma unroll
     for (int q = 0; q < VPL; ++q) {
       const float4 f = lane_on ? __ldg(fxv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-      fx[4 * q] = f.x;
-      fx[4 * q + 1] = f.y;
-      fx[4 * q + 2] = f.z;
-      fx[4 * q + 3] = f.w;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) fx[q * EPT + e] = reinterpret_cast<const E*>(&f)[e];
     }
   }
   const float s = (float)(*d.scale);
   const float dtg = d.dtg;
-  float* field = static_cast<float*>(d.field);
-  const float* fyz = static_cast<const float*>(d.fyz);
+  E* field = static_cast<E*>(d.field);
+  const E* fyz = static_cast<const E*>(d.fyz);
   const long long nel = (long long)d.ny * d.nz * pitch;
   const int npass = (it.nrow + RP - 1) / RP;
   auto row_of = [&](int q) { return it.row0 + (long long)q * RP + rp; };
@@ -1288,23 +1301,19 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_batch_x_reg(const __grid_co
   };
   float4 cur[VPL], nxt[VPL];
   load_row(0, cur);
-  float fr = valid(0) ? fyz[row_of(0)] : 0.f;
+  E fr = valid(0) ? fyz[row_of(0)] : F::zero();
   for (int q = 0; q < npass; ++q) {
-    float frn = fr;
+    E frn = fr;
     if (q + 1 < npass) {
       load_row(q + 1, nxt);
-      frn = valid(q + 1) ? fyz[row_of(q + 1)] : 0.f;
+      frn = valid(q + 1) ? fyz[row_of(q + 1)] : F::zero();
     }
-    float v[EPL];
+    E v[EPL];
 #pragma unroll
-    for (int qq = 0; qq < VPL; ++qq) {
-      v[4 * qq] = cur[qq].x * s;
-      v[4 * qq + 1] = cur[qq].y * s;
-      v[4 * qq + 2] = cur[qq].z * s;
-      v[4 * qq + 3] = cur[qq].w * s;
-    }
-    // the same operations in the same order as the copy-fed kernel (x_band_rows), so
-    // that a slot gets the same bits from either
+    for (int qq = 0; qq < VPL; ++qq)
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[qq * EPT + e] = F::scaled(reinterpret_cast<const E*>(&cur[qq])[e], s);
+    // (the argument dt g |v|^2 is formed again where it is used rather than held)
     float ymax = 0.f;
 #pragma unroll
     for (int e = 0; e < EPL; ++e) ymax = fmaxf(ymax, fabsf(dtg * F::abs2(v[e])));
@@ -1317,30 +1326,34 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_batch_x_reg(const __grid_co
 #pragma unroll
       for (int e = 0; e < EPL; ++e) v[e] = F::nonlinear_full(v[e], F::mul(fx[e], fr), dtg * F::abs2(v[e]));
     }
-    float lo[W + 1], hi[W + 1];
+    // halo: lo[m] = position x0 - m, hi[m] = position x0 + EPL - 1 + m (m = 1..W); odd
+    // images: position -m is 0 (m = 1) or -v[m - 2], position nx - 1 + m is 0 (m = 1)
+    // or -v[EPL + 1 - m]
+    E lo[W + 1], hi[W + 1];
 #pragma unroll
     for (int m = 1; m <= W; ++m) {
-      lo[m] = __shfl_up_sync(0xffffffffu, v[EPL - m], 1);
-      hi[m] = __shfl_down_sync(0xffffffffu, v[m - 1], 1);
-      if (first) lo[m] = m == 1 ? 0.f : -v[m - 2];
-      if (last) hi[m] = m == 1 ? 0.f : -v[EPL + 1 - m];
+      lo[m] = shfl_up_e(v[EPL - m], 1);
+      hi[m] = shfl_down_e(v[m - 1], 1);
+      if (first) lo[m] = m == 1 ? F::zero() : F::scaled(v[m - 2], -1.f);
+      if (last) hi[m] = m == 1 ? F::zero() : F::scaled(v[EPL + 1 - m], -1.f);
     }
-    auto win = [&](int j) -> float { return j < 0 ? lo[-j] : (j >= EPL ? hi[j - EPL + 1] : v[j]); };
+    auto win = [&](int j) -> E { return j < 0 ? lo[-j] : (j >= EPL ? hi[j - EPL + 1] : v[j]); };
     const long long r = row_of(q);
     const bool store = valid(q) && GP_IN(r * pitch + x0 + EPL - 1, nel, b.status);
     float4* dst = reinterpret_cast<float4*>(field + (size_t)(store ? r : 0) * pitch + x0);
 #pragma unroll
     for (int qq = 0; qq < VPL; ++qq) {
-      float o[4];
+      float4 ov;
+      E* o = reinterpret_cast<E*>(&ov);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int e = 4 * qq + t;
-        float acc = wt[0] * v[e];
+      for (int t = 0; t < EPT; ++t) {
+        const int e = EPT * qq + t;
+        E acc = F::mul(wt[0], v[e]);
 #pragma unroll
-        for (int k = 1; k <= W; ++k) acc = fmaf(wt[k], win(e - k) + win(e + k), acc);
-        o[t] = v[e] + acc;
+        for (int k = 1; k <= W; ++k) acc = F::chain(wt[k], F::add(win(e - k), win(e + k)), acc);
+        o[t] = F::add(v[e], acc);
       }
-      if (store) dst[qq] = make_float4(o[0], o[1], o[2], o[3]);
+      if (store) dst[qq] = ov;
     }
 #pragma unroll
     for (int qq = 0; qq < VPL; ++qq) cur[qq] = nxt[qq];
@@ -1384,9 +1397,12 @@ __device__ __forceinline__ FF band_line_thread(const LineArgs<typename Field<R, 
   const E* wt = p.wt;
   FF acc = FF{0.f, 0.f};
   if (t < (long long)nvec * nother * nseg) {
-    const int xv = (int)(t % nvec);
-    const long long rest = t / nvec;
-    const int o = (int)(rest % nother), sg = (int)(rest / nother);
+    // t < nvec * nother * nseg <= 1024 * 2048 * 293 < 2^31 (extents <= 2048, segments
+    // of at least 2W + 1 >= 7 points): 32-bit division, not 64-bit
+    const unsigned int tu = (unsigned int)t;
+    const int xv = (int)(tu % (unsigned int)nvec);
+    const unsigned int rest = tu / (unsigned int)nvec;
+    const int o = (int)(rest % (unsigned int)nother), sg = (int)(rest / (unsigned int)nother);
     const size_t pitch = (size_t)p.pitch;
     const size_t base = (AXIS == 1 ? (size_t)o * p.ny * pitch : (size_t)o * pitch) + (size_t)xv * EPT;
     const float4* in = reinterpret_cast<const float4*>(p.psi + base);
@@ -1481,9 +1497,12 @@ __device__ __forceinline__ FF band_line_thread_cp(const LineArgs<typename Field<
   const int bt = blockDim.x, tid = threadIdx.x;
   FF acc = FF{0.f, 0.f};
   if (t < (long long)nvec * nother * nseg) {
-    const int xv = (int)(t % nvec);
-    const long long rest = t / nvec;
-    const int o = (int)(rest % nother), sg = (int)(rest / nother);
+    // t < nvec * nother * nseg <= 1024 * 2048 * 293 < 2^31 (extents <= 2048, segments
+    // of at least 2W + 1 >= 7 points): 32-bit division, not 64-bit
+    const unsigned int tu = (unsigned int)t;
+    const int xv = (int)(tu % (unsigned int)nvec);
+    const unsigned int rest = tu / (unsigned int)nvec;
+    const int o = (int)(rest % (unsigned int)nother), sg = (int)(rest / (unsigned int)nother);
     const size_t pitch = (size_t)p.pitch;
     const size_t base = (AXIS == 1 ? (size_t)o * p.ny * pitch : (size_t)o * pitch) + (size_t)xv * EPT;
     const float4* in = reinterpret_cast<const float4*>(p.psi + base);
@@ -1582,6 +1601,8 @@ __device__ __forceinline__ FF band_line_thread_cp(const LineArgs<typename Field<
 template <class R, bool CPLX, int AXIS, bool NORM, int W, bool CP>
 __global__ void __launch_bounds__(128) k_sweep_band_line(const __grid_constant__ SweepParams p) {
   pdl_begin();
+  // the factor's dither (FP32, imaginary time): the step's x sweep has read the counter
+  if (AXIS == 1 && p.step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *p.step_ctr += 1;
   using E = typename Field<R, CPLX>::E;
   LineArgs<E> a;
   a.psi = static_cast<const E*>(p.psi);
@@ -1922,7 +1943,8 @@ static cudaError_t launch_batch_W(int axis, const BatchArgs& b, bool cplx, int g
                                   cudaStream_t st) {
   if (axis == 0 && b.x_reg) {
     if constexpr (W <= 7)
-      if (!cplx) return launch_pdl(k_batch_x_reg<W>, grid, 32 * kXRegWarps, 0, st, b);
+      return cplx ? launch_pdl(k_batch_x_reg<true, W>, grid, 32 * kXRegWarps, 0, st, b)
+                  : launch_pdl(k_batch_x_reg<false, W>, grid, 32 * kXRegWarps, 0, st, b);
     return cudaErrorInvalidValue;
   }
   if (axis == 0)
@@ -1936,8 +1958,15 @@ static cudaError_t launch_batch_W(int axis, const BatchArgs& b, bool cplx, int g
               : launch_pdl(k_batch_band_line<float, false, 2, true, W>, grid, 128, ysmem, st, b);
 }
 
-cudaError_t batch_x_reg_prepare(int w, int* blocks_per_sm) {
-  void (*k)(BatchArgs) = w == 3 ? k_batch_x_reg<3> : w == 5 ? k_batch_x_reg<5> : nullptr;
+bool batch_x_reg_fits(int nx, int w, bool complex_field) {
+  const int epl = complex_field ? 8 : 16;
+  return nx % epl == 0 && nx <= 32 * epl && (w == 3 || w == 5);
+}
+
+cudaError_t batch_x_reg_prepare(int w, bool complex_field, int* blocks_per_sm) {
+  void (*k)(BatchArgs) = nullptr;
+  if (w == 3) k = complex_field ? k_batch_x_reg<true, 3> : k_batch_x_reg<false, 3>;
+  if (w == 5) k = complex_field ? k_batch_x_reg<true, 5> : k_batch_x_reg<false, 5>;
   if (!k) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * kXRegWarps, 0);
 }

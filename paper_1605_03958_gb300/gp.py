@@ -536,6 +536,7 @@ def gp_pool_info(pool) -> dict:
             "free_bytes", "largest_free")
     d = dict(zip(keys, list(v)))
     d["x_reg"] = (d["graph"] >> 1) & 1
+    d["x_reg_complex"] = (d["graph"] >> 2) & 1
     d["graph"] &= 1
     return d
 

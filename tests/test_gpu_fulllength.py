@@ -150,7 +150,9 @@ def test_c2_g0_exact_fixed_point_fp32(P):
     s.close()
     want = exact_fixed_point_g0()
     d_got, d_ref = psi.astype(np.float64) ** 2, want ** 2
-    assert np.sqrt(np.sum((d_got - d_ref) ** 2) / np.sum(d_ref ** 2)) <= 1e-5
+    l2 = np.sqrt(np.sum((d_got - d_ref) ** 2) / np.sum(d_ref ** 2))
+    print("FP32 g = 0 after 10^4 steps, density relative L2 against the exact fixed point:", l2)
+    assert l2 <= 1e-5
 
 
 @pytest.mark.parametrize("g", [0, 100, 2000])
@@ -162,14 +164,17 @@ def test_c2_ground_state_fp32_full_length(P, g):
     dens = [s.density1d(a) for a in range(3)]
     s.close()
     want = fx["observables"]
-    assert rel(o["mu"], want["mu"]) <= 1e-5, (o["mu"], want["mu"])
     d_got = np.abs(samples(psi, fx)) ** 2
     d_ref = np.abs(unpack(fx["psi_samples"])) ** 2
     l2 = np.sqrt(np.sum((d_got - d_ref) ** 2) / np.sum(d_ref ** 2))
+    l2_1d = [np.sqrt(np.sum((dens[a] - unpack(fx["density1d"][a])) ** 2) /
+                     np.sum(unpack(fx["density1d"][a]) ** 2)) for a in range(3)]
+    print(f"FP32 g = {g}: mu relative {rel(o['mu'], want['mu']):.2e}, density relative L2 "
+          f"{l2:.2e} (samples), {max(l2_1d):.2e} (1D densities)")
+    assert rel(o["mu"], want["mu"]) <= 1e-5, (o["mu"], want["mu"])
     assert l2 <= 1e-5, l2
     for a in range(3):
-        ref = unpack(fx["density1d"][a])
-        assert np.sqrt(np.sum((dens[a] - ref) ** 2) / np.sum(ref ** 2)) <= 1e-5, a
+        assert l2_1d[a] <= 1e-5, a
 
 
 def quench(P, fx, prec):

@@ -443,8 +443,8 @@ def test_fp32_host_io_matches_fp64_host_io(P, orc, mode):
 def test_fp32_overlapped_read_equals_synchronous_read(P, orc, mode, nx):
     """gp_get_psi_f32_async (snapshot on the device, copy on the solver's copy stream,
     complete after gp_sync) against gp_get_psi_f32, contiguous (nx = 40) and padded
-    (nx = 37) rows: the same bits; the solver's state is untouched by the overlapped
-    read, and a put / step / read loop — each read's copy running beside the next put
+    (nx = 37) rows: the same bits; neither read changes the solver's state (later
+    steps give the same bits), and a put / step / read loop — each read's copy running beside the next put
     and step — gives the same bits as the synchronous loop."""
     import torch
     p = problem(orc, nx, 29, 23, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=80.0)
@@ -462,7 +462,7 @@ def test_fp32_overlapped_read_equals_synchronous_read(P, orc, mode, nx):
     want = P.gp.gp_get_psi_f32(b.handle, p.shape, cplx)
     got = host.numpy().view(np.complex64 if cplx else np.float32).reshape(p.shape)
     assert np.array_equal(got, want)
-    # a continues without the fold the synchronous read made in b: same bits
+    # neither read changes the solver: both continue with the same bits
     for s in (a, b):
         s.step_imag(4) if mode == "imag" else s.step_real(4)
     assert np.array_equal(P.gp.gp_get_psi_f32(a.handle, p.shape, cplx),

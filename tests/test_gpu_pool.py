@@ -200,3 +200,55 @@ def test_pool_register_row_x_gives_the_copy_fed_bits(P, monkeypatch):
     assert outs["1"][1] == 1 and outs["0"][1] == 0
     for a, b in zip(outs["1"][0], outs["0"][0]):
         assert np.array_equal(a, b)
+
+
+# complex slots whose rows are 8 m <= 256 points (the register-row x sweep's condition)
+CSLOTS = [
+    dict(nx=48, ny=32, nz=24, gamma=1.0, nu=1.4, lam=2.2, g=30.0),
+    dict(nx=128, ny=20, nz=18, gamma=0.7, nu=1.9, lam=1.2, g=400.0),
+    dict(nx=32, ny=16, nz=24, gamma=2.5, nu=0.8, lam=1.6, g=5.0),
+]
+
+
+def quench_pool(P, slots, steps_imag=10, steps_real=20):
+    """steps_imag imaginary steps, then every slot to real time at twice its g."""
+    pool, ids = make_pool(P, slots)
+    pool.step(steps_imag)
+    for s, d in zip(ids, slots):
+        pool.set_real_time(s)
+        pool.set_g(s, 2 * d["g"])
+    pool.step(steps_real)
+    return pool, ids
+
+
+def test_pool_complex_register_row_x_sweep(P, orc, monkeypatch):
+    """Real-time slots with rows of 8 m complex points run the x sweep with rows in
+    registers (8 complex points per lane, several rows per warp pass); it and the
+    copy-fed x sweep both follow the oracle's quench at the FP32 tolerance."""
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GP_X_REG", flag)
+        pool, ids = quench_pool(P, CSLOTS)
+        outs[flag] = ([pool.get_psi(s, as_complex=True) for s in ids], pool.info()["x_reg_complex"])
+        pool.close()
+    monkeypatch.delenv("GP_X_REG", raising=False)
+    assert outs["1"][1] == 1 and outs["0"][1] == 0
+    for k, d in enumerate(CSLOTS):
+        p = oracle_problem(orc, d)
+        psi = orc.step_imag(p, orc.init_gaussian(p), 10).astype(complex)
+        ref = orc.step_real(oracle_problem(orc, dict(d, g=2 * d["g"])), psi, 20)
+        tol = 3e-6 * np.max(np.abs(ref))
+        for flag in ("1", "0"):
+            assert np.max(np.abs(outs[flag][0][k] - ref)) <= tol, (d, flag)
+
+
+def test_pool_complex_slot_alone_equals_slot_in_mix(P):
+    """The register-row x sweep chooses the pointwise polynomial per row, so a complex
+    slot gives the same bits alone and in a mix of other complex grids."""
+    mix, ids = quench_pool(P, CSLOTS)
+    assert mix.info()["x_reg_complex"] == 1
+    for d, s in zip(CSLOTS, ids):
+        alone, (a,) = quench_pool(P, [d])
+        assert np.array_equal(alone.get_psi(a, as_complex=True), mix.get_psi(s, as_complex=True)), d
+        alone.close()
+    mix.close()
