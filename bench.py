@@ -345,6 +345,39 @@ def paper_precision(P, args, flush, hbm, sm_mhz):
     return out
 
 
+def link_bandwidth(host_in, host_out, reps=10):
+    """Host-device copy rates of the e2e loop's pinned buffers (one field each way):
+    host-to-device alone, device-to-host alone, and both at once on two streams (GB/s
+    per direction), CUDA events around each repetition set."""
+    import torch
+    n = host_in.numel()
+    d_a = torch.empty(n, dtype=host_in.dtype, device="cuda")
+    d_b = torch.zeros(n, dtype=host_in.dtype, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nbytes = n * host_in.element_size()
+
+    def rate(h2d, d2h):
+        def once():
+            if h2d:
+                with torch.cuda.stream(s1):
+                    d_a.copy_(host_in, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    host_out.copy_(d_b, non_blocking=True)
+        once()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            once()
+        torch.cuda.synchronize()
+        return round(nbytes * reps / (time.perf_counter() - t0) / 1e9, 1)
+
+    out = {"bytes": nbytes, "h2d_gbs": rate(True, False), "d2h_gbs": rate(False, True),
+           "both_per_direction_gbs": rate(True, True)}
+    del d_a, d_b
+    return out
+
+
 def dram_bound(P, args, flush, hbm):
     """The same FP32 imaginary-time step on 512 x 400 x 320 (a 262 MB field, twice the
     L2): every sweep streams from and to DRAM."""
@@ -610,36 +643,46 @@ def run_cuda(args):
     if args.e2e_steps > 0:
         f32 = args.prec == "f32"
         hdt = torch.float32 if f32 else torch.float64
-        put = P.gp.gp_set_psi_f32_ptr if f32 else P.gp.gp_set_psi_ptr
         get = P.gp.gp_get_psi_f32_async_ptr if f32 else P.gp.gp_get_psi_ptr
         nh = NPTS * (2 if real else 1)
         host_in = torch.empty(nh, dtype=hdt, pin_memory=True)
         host_out = torch.empty(nh, dtype=hdt, pin_memory=True)
         get(s.handle, host_in.data_ptr(), real)
         P.gp.gp_sync(s.handle)
-        for _ in range(3):
-            put(s.handle, host_in.data_ptr(), real)
-            step(1)
-            get(s.handle, host_out.data_ptr(), real)
-        P.gp.gp_sync(s.handle)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            put(s.handle, host_in.data_ptr(), real)
-            step(1)
-            get(s.handle, host_out.data_ptr(), real)
-        P.gp.gp_sync(s.handle)
-        torch.cuda.synchronize()
-        barrier()
-        e2e_s = max_over_ranks(time.perf_counter() - t0)
+
+        def e2e_run(put, nsteps):
+            for _ in range(3):
+                put(s.handle, host_in.data_ptr(), real)
+                step(1)
+                get(s.handle, host_out.data_ptr(), real)
+            P.gp.gp_sync(s.handle)
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(nsteps):
+                put(s.handle, host_in.data_ptr(), real)
+                step(1)
+                get(s.handle, host_out.data_ptr(), real)
+            P.gp.gp_sync(s.handle)
+            torch.cuda.synchronize()
+            barrier()
+            return max_over_ranks(time.perf_counter() - t0)
+
+        # FP32: the overlapped write (its host-to-device copy beside the previous step
+        # and the previous read's packing) and, for comparison, the synchronous one
+        put = P.gp.gp_set_psi_f32_async_ptr if f32 else P.gp.gp_set_psi_ptr
+        e2e_s = e2e_run(put, args.e2e_steps)
         name = "_f32" if f32 else ""
         e2e = {"value": round(world * NPTS * args.e2e_steps / e2e_s, 1), "unit": "grid-point-steps/s",
                "h2d_bytes_per_step": NPTS * sbytes, "d2h_bytes_per_step": NPTS * sbytes,
                "steps": args.e2e_steps,
-               "api": (f"gp_set_psi{name}(pinned host field) + gp_step_{args.mode}(1) + "
-                       f"gp_get_psi{name}{'_async' if f32 else ''}(pinned)"
+               "api": (f"gp_set_psi{name}{'_async' if f32 else ''}(pinned host field) + "
+                       f"gp_step_{args.mode}(1) + gp_get_psi{name}{'_async' if f32 else ''}(pinned)"
                        + ("; gp_sync after the last step" if f32 else ""))}
+        if f32:
+            e2e["value_synchronous_write"] = round(
+                world * NPTS * args.e2e_steps / e2e_run(P.gp.gp_set_psi_f32_ptr, args.e2e_steps), 1)
+        e2e["link"] = link_bandwidth(host_in, host_out)
 
     # context: the same step back to back with L2 kept warm (no flush), one call
     torch.cuda.synchronize()

@@ -154,19 +154,35 @@ int gp_get_psi_f32(gp_solver* s, float* host, int as_complex);
 
 /* Overlapped read of an FP32 solver's field into host (same layout as
  * gp_get_psi_f32).  The field times the pending renormalisation factor is packed on
- * the device into a snapshot buffer of the solver (8 bytes per grid point,
- * cudaMalloc'd on the first call and freed by gp_destroy; the solver's state is left
- * as it is), and the device-to-host copy of the snapshot runs on the solver's own
- * copy stream: it overlaps whatever the caller enqueues next — the next
- * gp_set_psi_f32, whose host-to-device copy runs in the other direction at the same
- * time, and the next steps.  The next overlapped read waits for the previous copy
- * before it packs; gp_sync(s) waits for it too, and so do the synchronous reads,
- * observables and densities.  host is complete only after gp_sync(s) (or
- * gp_destroy); it should be page-locked for the copy to be asynchronous.  Does not
- * read the status flag (gp_sync does).  Same argument errors as gp_get_psi_f32;
- * GP_ERR_NOMEM if the snapshot buffer cannot be allocated, GP_ERR_CUDA if the copy
- * stream cannot be created.                                                        */
+ * the device into one of two snapshot buffers of the solver, taken in turn (16 bytes
+ * per grid point in all, cudaMalloc'd on the first call and freed by gp_destroy; the
+ * solver's state is left as it is), and the device-to-host copy of the snapshot runs
+ * on the solver's own copy stream: it overlaps whatever the caller enqueues next —
+ * the next write (gp_set_psi_f32_async's host-to-device copy runs in the other
+ * direction at the same time), the next steps and the next read's packing.  A read
+ * waits, before it packs, for the copy of the read two before it (same buffer);
+ * gp_sync(s) waits for all of them, and so do the synchronous reads, observables and
+ * densities.  host is complete only after gp_sync(s) (or gp_destroy); it should be
+ * page-locked for the copy to be asynchronous.  Does not read the status flag
+ * (gp_sync does).  Same argument errors as gp_get_psi_f32; GP_ERR_NOMEM if the
+ * snapshot buffers cannot be allocated, GP_ERR_CUDA if the copy stream cannot be
+ * created.                                                                          */
 int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex);
+
+/* Overlapped write of an FP32 solver's field from host (same layout and arguments as
+ * gp_set_psi_f32).  The host-to-device copy runs on the solver's own put stream into
+ * one of two buffers of the solver, taken in turn (16 bytes per grid point in all,
+ * cudaMalloc'd on the first call and freed by gp_destroy), beside whatever the solver
+ * stream is doing (the steps and the packing of an overlapped read of the previous
+ * field); the next call that reads or
+ * writes the field (steps, reads, observables, densities, gp_sync, another write)
+ * first waits for that copy and moves the buffer into the field on the solver stream,
+ * with the effect of gp_set_psi_f32 (factor 1, step count 0).  host (page-locked for
+ * the copy to overlap) must stay unchanged until a synchronising call (gp_sync, a
+ * synchronous read, gp_observables, a density) has returned.  Same argument errors as
+ * gp_set_psi_f32; GP_ERR_NOMEM if the buffer cannot be allocated, GP_ERR_CUDA if the
+ * put stream cannot be created.                                                     */
+int gp_set_psi_f32_async(gp_solver* s, const float* host, int is_complex);
 
 /* nsteps imaginary-time SSCN steps on the real field, each renormalised to unit
  * norm.  GP_ERR_STATE on a complex field.  Asynchronous.  A call of one step

@@ -330,13 +330,25 @@ struct gp_solver {
   cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
   cudaGraphExec_t strang_exec[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
-  // overlapped field reads (gp_get_psi_f32_async): the field is packed into export_buf
-  // (allocated on first use) and copied to host on copy_stream; the next packing and the
-  // host-completing calls wait for copy_done
+  // overlapped field reads (gp_get_psi_f32_async): the field is packed into one of the
+  // two halves of export_buf (allocated on first use, the halves taken in turn) and
+  // copied to host on copy_stream; a packing into a half waits for that half's previous
+  // copy (copy_done[half]), the host-completing calls for both
   void* export_buf = nullptr;
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t copy_ready = nullptr, copy_done = nullptr;
-  bool copy_pending = false;
+  cudaEvent_t copy_ready = nullptr, copy_done[2] = {nullptr, nullptr};
+  bool copy_pending[2] = {false, false};
+  int export_next = 0;
+  // overlapped field writes (gp_set_psi_f32_async): the host field is copied into
+  // one of the two halves of put_buf (allocated on first use, the halves taken in turn)
+  // on put_stream; the next call that touches the field waits for put_ready, moves the
+  // half into the field on the solver stream and records that half's put_free, which
+  // the write after next waits for before it reuses the half
+  void* put_buf = nullptr;
+  cudaStream_t put_stream = nullptr;
+  cudaEvent_t put_ready = nullptr, put_free[2] = {nullptr, nullptr};
+  bool put_pending = false, put_complex = false;
+  int put_half = 0, put_next = 0;
   bool step_graph = true;            // false once capture failed: direct launches only
   // timing
   bool timing = false;
@@ -1088,9 +1100,33 @@ template <class R> int steps(gp_solver* s, long nsteps) {
 
 // Make the solver's stream wait for an overlapped read still copying its snapshot.
 void wait_copies(gp_solver* s) {
-  if (!s->copy_pending) return;
-  cudaStreamWaitEvent(s->stream, s->copy_done, 0);
-  s->copy_pending = false;
+  for (int h = 0; h < 2; ++h)
+    if (s->copy_pending[h]) {
+      cudaStreamWaitEvent(s->stream, s->copy_done[h], 0);
+      s->copy_pending[h] = false;
+    }
+}
+
+int set_scale_one(gp_solver* s);
+int reset_steps(gp_solver* s);
+
+// The field of a pending overlapped write (gp_set_psi_f32_async) into the solver: the
+// solver stream waits for its host-to-device copy, moves it from its half of put_buf
+// into the field (pitched rows, pad columns zero) and frees that half.  Every call
+// that reads or writes the field runs this first.
+int take_put(gp_solver* s) {
+  if (!s->put_pending) return GP_OK;
+  s->put_pending = false;
+  GP_CUDA(s, cudaStreamWaitEvent(s->stream, s->put_ready, 0));
+  s->is_complex = s->put_complex;
+  FieldParams f = field_params(s);
+  f.psi = s->field;
+  const size_t npts = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
+  const float* src = static_cast<const float*>(s->put_buf) + (size_t)s->put_half * 2 * npts;
+  GP_CUDA(s, gpk::launch_import_f32(f, s->is_complex, src, s->stream));
+  GP_CUDA(s, cudaEventRecord(s->put_free[s->put_half], s->stream));
+  const int rc = set_scale_one(s);
+  return rc != GP_OK ? rc : reset_steps(s);
 }
 
 int check_status(gp_solver* s) {
@@ -1189,8 +1225,17 @@ void gp_destroy(gp_solver* s) {
     cudaStreamDestroy(s->copy_stream);
   }
   if (s->copy_ready) cudaEventDestroy(s->copy_ready);
-  if (s->copy_done) cudaEventDestroy(s->copy_done);
+  for (auto ev : s->copy_done)
+    if (ev) cudaEventDestroy(ev);
   if (s->export_buf) cudaFree(s->export_buf);
+  if (s->put_stream) {
+    cudaStreamSynchronize(s->put_stream);
+    cudaStreamDestroy(s->put_stream);
+  }
+  if (s->put_ready) cudaEventDestroy(s->put_ready);
+  for (auto ev : s->put_free)
+    if (ev) cudaEventDestroy(ev);
+  if (s->put_buf) cudaFree(s->put_buf);
   for (auto& t : s->pending) {
     cudaEventDestroy(t.start);
     cudaEventDestroy(t.stop);
@@ -1204,6 +1249,7 @@ void gp_destroy(gp_solver* s) {
 
 int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
   if (!s) return GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   if (!(wx > 0) || !(wy > 0) || !(wz > 0) || !std::isfinite(wx) || !std::isfinite(wy) ||
       !std::isfinite(wz))
     return fail(s, GP_ERR_ARG, "Gaussian frequencies must be finite and > 0");
@@ -1221,6 +1267,7 @@ int gp_init_gaussian(gp_solver* s, double wx, double wy, double wz) {
 
 int gp_set_psi(gp_solver* s, const double* host, int is_complex) {
   if (!s || !host || (is_complex != 0 && is_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   const size_t N = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
   GP_CUDA(s, cudaMemcpyAsync(s->staging, host, N * 8 * (is_complex ? 2 : 1),
                              cudaMemcpyHostToDevice, s->stream));
@@ -1235,6 +1282,7 @@ int gp_set_psi(gp_solver* s, const double* host, int is_complex) {
 
 int gp_get_psi(gp_solver* s, double* host, int as_complex) {
   if (!s || !host || (as_complex != 0 && as_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   if (s->is_complex && !as_complex)
     return fail(s, GP_ERR_STATE, "the field is complex; request it with as_complex = 1");
   wait_copies(s);
@@ -1252,6 +1300,7 @@ int gp_get_psi(gp_solver* s, double* host, int as_complex) {
 int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex) {
   if (!s || !host || (is_complex != 0 && is_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
   if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_set_psi");
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   s->is_complex = is_complex == 1;
   const int m = is_complex;
   const size_t eb = (size_t)4 * (m + 1), pitch = (size_t)s->L.pitch[m] * eb, row = (size_t)s->prm.nx * eb;
@@ -1269,9 +1318,53 @@ int gp_set_psi_f32(gp_solver* s, const float* host, int is_complex) {
   return rc != GP_OK ? rc : reset_steps(s);
 }
 
+int gp_set_psi_f32_async(gp_solver* s, const float* host, int is_complex) {
+  if (!s || !host || (is_complex != 0 && is_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_set_psi");
+  if (!s->put_stream) {   // the put stream and its three events, all or none
+    cudaStream_t ps = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+      if (ps) cudaStreamDestroy(ps);
+      return cuda_fail(s, e, "put stream");
+    }
+    s->put_stream = ps;
+    s->put_ready = ev[0];
+    s->put_free[0] = ev[1];
+    s->put_free[1] = ev[2];
+    GP_CUDA(s, cudaEventRecord(s->put_free[0], s->stream));
+    GP_CUDA(s, cudaEventRecord(s->put_free[1], s->stream));
+  }
+  const size_t npts = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
+  if (!s->put_buf && cudaMalloc(&s->put_buf, 16 * npts) != cudaSuccess) {   // two packed complex fields
+    cudaGetLastError();
+    s->put_buf = nullptr;
+    return fail(s, GP_ERR_NOMEM, "no device memory for the buffers of overlapped writes");
+  }
+  // a write still waiting to be taken is superseded: take it first
+  int rc = take_put(s);
+  if (rc != GP_OK) return rc;
+  const int h = s->put_next;
+  s->put_next ^= 1;
+  GP_CUDA(s, cudaStreamWaitEvent(s->put_stream, s->put_free[h], 0));   // its half was moved
+  float* dst = static_cast<float*>(s->put_buf) + (size_t)h * 2 * npts;
+  GP_CUDA(s, cudaMemcpyAsync(dst, host, (size_t)4 * (is_complex + 1) * npts, cudaMemcpyHostToDevice,
+                             s->put_stream));
+  GP_CUDA(s, cudaEventRecord(s->put_ready, s->put_stream));
+  s->put_pending = true;
+  s->put_complex = is_complex == 1;
+  s->put_half = h;
+  return GP_OK;
+}
+
 int gp_get_psi_f32(gp_solver* s, float* host, int as_complex) {
   if (!s || !host || (as_complex != 0 && as_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
   if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_get_psi");
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   if (as_complex != (s->is_complex ? 1 : 0))
     return fail(s, GP_ERR_STATE, "as_complex must match the field (0: real, 1: complex)");
   wait_copies(s);
@@ -1289,46 +1382,54 @@ int gp_get_psi_f32(gp_solver* s, float* host, int as_complex) {
 int gp_get_psi_f32_async(gp_solver* s, float* host, int as_complex) {
   if (!s || !host || (as_complex != 0 && as_complex != 1)) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
   if (is_f64(s)) return fail(s, GP_ERR_ARG, "FP32 host I/O needs an FP32 solver; use gp_get_psi");
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   if (as_complex != (s->is_complex ? 1 : 0))
     return fail(s, GP_ERR_STATE, "as_complex must match the field (0: real, 1: complex)");
-  if (!s->copy_stream) {   // the copy stream and its two events, all or none
+  if (!s->copy_stream) {   // the copy stream and its three events, all or none
     cudaStream_t cs = nullptr;
-    cudaEvent_t ready = nullptr, done = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
     if (e != cudaSuccess) {
-      if (done) cudaEventDestroy(done);
-      if (ready) cudaEventDestroy(ready);
+      for (auto x : ev)
+        if (x) cudaEventDestroy(x);
       if (cs) cudaStreamDestroy(cs);
       return cuda_fail(s, e, "copy stream");
     }
     s->copy_stream = cs;
-    s->copy_ready = ready;
-    s->copy_done = done;
+    s->copy_ready = ev[0];
+    s->copy_done[0] = ev[1];
+    s->copy_done[1] = ev[2];
   }
   const size_t npts = (size_t)s->prm.nx * s->prm.ny * s->prm.nz;
-  if (!s->export_buf && cudaMalloc(&s->export_buf, 8 * npts) != cudaSuccess) {   // a packed complex field
+  if (!s->export_buf && cudaMalloc(&s->export_buf, 16 * npts) != cudaSuccess) {   // two packed complex fields
     cudaGetLastError();
     s->export_buf = nullptr;
-    return fail(s, GP_ERR_NOMEM, "no device memory for the snapshot of an overlapped read");
+    return fail(s, GP_ERR_NOMEM, "no device memory for the snapshots of overlapped reads");
   }
-  wait_copies(s);   // the previous overlapped read may still be copying the snapshot
+  // this read's half of the snapshot buffer; its previous read may still be copying
+  const int h = s->export_next;
+  s->export_next ^= 1;
+  if (s->copy_pending[h]) {
+    GP_CUDA(s, cudaStreamWaitEvent(s->stream, s->copy_done[h], 0));
+    s->copy_pending[h] = false;
+  }
   const int m = as_complex;
   const size_t bytes = (size_t)4 * (m + 1) * npts;
-  float* snap = static_cast<float*>(s->export_buf);
+  float* snap = static_cast<float*>(s->export_buf) + (size_t)h * 2 * npts;
   const cudaError_t e = gpk::launch_export_f32(field_params(s), m == 1, snap, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "export");
   GP_CUDA(s, cudaEventRecord(s->copy_ready, s->stream));
   GP_CUDA(s, cudaStreamWaitEvent(s->copy_stream, s->copy_ready, 0));
   GP_CUDA(s, cudaMemcpyAsync(host, snap, bytes, cudaMemcpyDeviceToHost, s->copy_stream));
-  GP_CUDA(s, cudaEventRecord(s->copy_done, s->copy_stream));
-  s->copy_pending = true;
+  GP_CUDA(s, cudaEventRecord(s->copy_done[h], s->copy_stream));
+  s->copy_pending[h] = true;
   return GP_OK;
 }
 
 int gp_step_imag(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   if (s->is_complex) return fail(s, GP_ERR_STATE, "imaginary-time steps need a real field");
   NvtxRange range("gp_step_imag");
   return is_f64(s) ? steps<double>(s, nsteps) : steps<float>(s, nsteps);
@@ -1336,6 +1437,7 @@ int gp_step_imag(gp_solver* s, long nsteps) {
 
 int gp_step_real(gp_solver* s, long nsteps) {
   if (!s || nsteps < 0) return s ? fail(s, GP_ERR_ARG, "nsteps must be >= 0") : GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   if (!s->is_complex) {
     const int rc = promote_to_complex(s);
     if (rc != GP_OK) return rc;
@@ -1385,6 +1487,7 @@ int gp_get_g(const gp_solver* s, double* g) {
 
 int gp_observables(gp_solver* s, gp_obs* out) {
   if (!s || !out) return s ? fail(s, GP_ERR_ARG, "out is NULL") : GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   wait_copies(s);
   const FieldParams f = field_params(s);
   cudaError_t e = is_f64(s) ? gpk::launch_observables<double>(f, s->is_complex, s->stream)
@@ -1409,6 +1512,7 @@ int gp_observables(gp_solver* s, gp_obs* out) {
 
 int gp_density2d(gp_solver* s, int plane, double* out) {
   if (!s || !out || plane < 0 || plane > 2) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   wait_copies(s);
   const gp_params& p = s->prm;
   const FieldParams f = field_params(s);
@@ -1423,6 +1527,7 @@ int gp_density2d(gp_solver* s, int plane, double* out) {
 
 int gp_density1d(gp_solver* s, int axis, double* out) {
   if (!s || !out || axis < 0 || axis > 2) return s ? fail(s, GP_ERR_ARG, "bad arguments") : GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   wait_copies(s);
   const gp_params& p = s->prm;
   const FieldParams f = field_params(s);
@@ -1445,6 +1550,7 @@ int gp_density1d(gp_solver* s, int axis, double* out) {
 
 int gp_sync(gp_solver* s) {
   if (!s) return GP_ERR_ARG;
+  if (const int rc_ = take_put(s)) return rc_;   // a pending overlapped write first
   wait_copies(s);
   resolve_scale(s);   // a deferred norm's non-finite flag is set where it is summed
   return check_status(s);

@@ -421,6 +421,13 @@ __device__ __forceinline__ double step_dither(const unsigned int* ctr) {
   const unsigned int u = *ctr * 0x9E3779B9u;
   return 1.0 + (double)(int)u * 0x1p-51;
 }
+// The same factor in FP32 (its steps of 2^-23 near 1), for kernels whose every thread
+// forms the factor: no FP64 arithmetic, which is slow on this part.
+__device__ __forceinline__ float step_dither_f(const unsigned int* ctr) {
+  if (!ctr) return 1.f;
+  const unsigned int u = *ctr * 0x9E3779B9u;
+  return 1.f + (float)(int)u * 0x1p-51f;
+}
 
 template <class R, bool CPLX> struct Field;
 

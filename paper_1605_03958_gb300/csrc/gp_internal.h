@@ -252,6 +252,9 @@ cudaError_t launch_resolve_scale(double* scale, int* state, const double* partia
 // FP32 field times *p.scale, packed into rows of nx elements in dst (not aliasing the
 // field); the field and the factor are left as they are.
 cudaError_t launch_export_f32(const FieldParams& p, bool complex_field, float* dst, cudaStream_t st);
+// Packed rows of nx FP32 elements (real or complex pairs) from src into the field,
+// pad columns zero.
+cudaError_t launch_import_f32(const FieldParams& p, bool complex_field, const float* src, cudaStream_t st);
 template <class R> cudaError_t launch_init_gaussian(const FieldParams& p, double wx, double wy,
                                                     double wz, cudaStream_t st);
 template <class R> cudaError_t launch_import(const FieldParams& p, const double* src,

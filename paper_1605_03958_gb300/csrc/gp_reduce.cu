@@ -262,6 +262,24 @@ __global__ void k_export_f32(const FieldParams p, int words, float* __restrict__
     for (size_t i = threadIdx.x; i < rw; i += blockDim.x) dst[r * rw + i] = src[r * pw + i] * s;
 }
 
+// The reverse: packed rows of nx elements in src into the FP32 field (pad columns
+// zero), as they are (no factor).
+__global__ void k_import_f32(const FieldParams p, int words, const float* __restrict__ src) {
+  float* dst = static_cast<float*>(p.psi);
+  const size_t rw = (size_t)p.nx * words, pw = (size_t)p.pitch * words;
+  const size_t nrows = (size_t)p.ny * p.nz;
+  if (rw == pw && rw % 4 == 0) {
+    const size_t n4 = nrows * rw / 4;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+      d4[i] = s4[i];
+    return;
+  }
+  for (size_t r = blockIdx.x; r < nrows; r += gridDim.x)
+    for (size_t i = threadIdx.x; i < pw; i += blockDim.x) dst[r * pw + i] = i < rw ? src[r * rw + i] : 0.f;
+}
+
 // ------------------------------------------------------------ initial Gaussian
 
 template <class R>
@@ -439,6 +457,11 @@ cudaError_t launch_half_pointwise(const FieldParams& p, bool complex_field, cons
 
 cudaError_t launch_export_f32(const FieldParams& p, bool complex_field, float* dst, cudaStream_t st) {
   k_export_f32<<<grid_for_rows(p), 256, 0, st>>>(p, complex_field ? 2 : 1, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import_f32(const FieldParams& p, bool complex_field, const float* src, cudaStream_t st) {
+  k_import_f32<<<grid_for_rows(p), 256, 0, st>>>(p, complex_field ? 2 : 1, src);
   return cudaGetLastError();
 }
 

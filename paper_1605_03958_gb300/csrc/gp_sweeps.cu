@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(32) k_sweep_x(const SweepParams p) {
     const int k = (int)(r / p.ny);
     const E* fxt = static_cast<const E*>(p.band_fx);                      // trap factor along x
     const E fr = __ldg(static_cast<const E*>(p.band_fyz) + (size_t)k * p.ny + j);   // of this row
-    const R s = (R)(*p.scale * step_dither(p.step_ctr));
+    const R s = (R)(*p.scale) * (R)step_dither_f(p.step_ctr);
     const R dtg = (R)(p.dt * p.g);
     const E* A = static_cast<const E*>(p.A);
     const E* B = static_cast<const E*>(p.B);
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(32) k_sweep_x_stream(const SweepParams p) {
   const E* B = static_cast<const E*>(p.B);
   const E Ab = __ldg(A + nx - 1), Bb = __ldg(B + nx - 1);
   const R* vx = static_cast<const R*>(p.vx);
-  const R s = (R)(*p.scale * step_dither(p.step_ctr));
+  const R s = (R)(*p.scale) * (R)step_dither_f(p.step_ctr);
   const R dt = (R)p.dt, g = (R)p.g;
   const long long myrow = r0 + min(lane, rows - 1);
   const int jrow = (int)(myrow % p.ny), krow = (int)(myrow / p.ny);
@@ -705,7 +705,7 @@ template <class E> struct XRows {
   const E* fyz;          // trap factor per row
   const E* wt;           // w_{k-W}, k = 0 .. 2W (centre as w_0 - 1)
   const double* scale;   // pending renormalisation factor
-  double dither;         // its step dither (step_dither; 1 for none)
+  float dither;          // the step's dither of it (step_dither_f; 1 for none)
   int* status;
   unsigned long long wait_ns;   // limit of the first bounded wait on each row copy
   long long row0;
@@ -747,7 +747,7 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
   const float4* fx = a.fx;
   const E* fyz = a.fyz;
   const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
-  const R s = (R)(*a.scale * a.dither);
+  const R s = (R)(*a.scale) * (R)a.dither;
   const R dtg = (R)a.dtg;
   // row slot r of stage st
   auto slot_of = [&](int st, int r) { return slots + (size_t)(st * G + r) * se; };
@@ -903,7 +903,7 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
 #pragma unroll
   for (int c = 0; c < NC; ++c)
     fxc[c] = lane + 32 * c < nvec ? __ldg(fx + lane + 32 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
-  const R s = (R)(*a.scale * a.dither);
+  const R s = (R)(*a.scale) * (R)a.dither;
   const R dtg = (R)a.dtg;
   const bool pw = a.pw != 0;
   const E* fyz = a.fyz + a.row0;
@@ -1046,7 +1046,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.fyz = static_cast<const E*>(p.band_fyz);
   a.wt = reinterpret_cast<const E*>(p.band_wt);
   a.scale = defer ? &s_factor : p.scale;
-  a.dither = step_dither(p.step_ctr);
+  a.dither = step_dither_f(p.step_ctr);
   a.status = p.status;
   a.wait_ns = p.wait_ns;
   a.row0 = row0;
@@ -1179,11 +1179,18 @@ __global__ void __launch_bounds__(32 * kXRegWarps) k_sweep_x_reg(const __grid_co
     load_row(row0, cur);
     fr = fyz[row0];
   }
-  s = (float)((p.norm_defer
-                    ? deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks,
-                                     p.norm_blocks, p.dV, p.status, blockIdx.x == 0, p.scale_state, p.scale)
-                    : *p.scale) *
-              step_dither(p.step_ctr));
+  {
+    // one thread forms the factor with the step's dither (FP64 arithmetic is slow on
+    // this part), the block shares it
+    __shared__ float s_block;
+    const double f = p.norm_defer
+                         ? deferred_scale(p.partials + (size_t)(blockIdx.x % p.norm_copies) * p.norm_blocks,
+                                          p.norm_blocks, p.dV, p.status, blockIdx.x == 0, p.scale_state, p.scale)
+                         : 0.0;
+    if (threadIdx.x == 0) s_block = (float)((p.norm_defer ? f : *p.scale) * step_dither(p.step_ctr));
+    __syncthreads();
+    s = s_block;
+  }
   if (nrow == 0) return;
   for (int i = 0; i < nrow; ++i) {
     const long long r = row0 + i;
@@ -1222,7 +1229,7 @@ __global__ void __launch_bounds__(32 * kBatchXWarps) k_batch_x_band(const __grid
   a.fyz = static_cast<const E*>(d.fyz);
   a.wt = reinterpret_cast<const E*>(d.wt[0]) + (kBandHalfMax - W);
   a.scale = d.scale;
-  a.dither = 1.0;
+  a.dither = 1.f;
   a.status = b.status;
   a.wait_ns = b.wait_ns;
   a.row0 = it.row0;
@@ -1514,85 +1521,94 @@ __device__ __forceinline__ FF band_line_thread_cp(const LineArgs<typename Field<
     // input j of the odd extension about the ghosts -1 and n
     // 16-byte vectors of the field, and this line's first one (bounds checks)
     const long long nvec_all = (long long)p.nz * p.ny * (long long)pitch / EPT, v0 = (long long)(base / EPT);
-    auto ld = [&](int j) -> float4 {
-      if (interior || (j >= 0 && j < n))
-        return GP_IN(v0 + (long long)j * sv, nvec_all, p.status) ? in[(size_t)j * sv]
-                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j == -1 || j == n) return make_float4(0.f, 0.f, 0.f, 0.f);
-      const int m = j < 0 ? -2 - j : 2 * n - j;
-      const float4 v = GP_IN(v0 + (long long)m * sv, nvec_all, p.status) ? in[(size_t)m * sv]
-                                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-      return make_float4(-v.x, -v.y, -v.z, -v.w);
-    };
-    // copy of turn b's inputs j = b + u + W (u < P) into slot set h
-    auto issue = [&](int b, int h) {
+    // the segment; INTERIOR (no ghost or image within reach, and the vector wholly
+    // inside the field: the common case) is a compile-time constant in each of the two
+    // instantiations
+    auto run = [&](auto interior_c) {
+      constexpr bool INTERIOR = decltype(interior_c)::value;
+      auto ld = [&](int j) -> float4 {
+        if (INTERIOR || (j >= 0 && j < n))
+          return GP_IN(v0 + (long long)j * sv, nvec_all, p.status) ? in[(size_t)j * sv]
+                                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j == -1 || j == n) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const int m = j < 0 ? -2 - j : 2 * n - j;
+        const float4 v = GP_IN(v0 + (long long)m * sv, nvec_all, p.status) ? in[(size_t)m * sv]
+                                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        return make_float4(-v.x, -v.y, -v.z, -v.w);
+      };
+      // copy of turn b's inputs j = b + u + W (u < P) into slot set h
+      auto issue = [&](int b, int h) {
 #pragma unroll
-      for (int u = 0; u < P; ++u) {
-        const int j = b + u + W;
-        int src = j;
-        bool ok = true;
-        if (!interior) {
-          ok = b + u < j1 && j != -1 && j != n;
-          src = j < 0 ? -2 - j : (j > n ? 2 * n - j : j);
-          if (!ok) src = 0;
+        for (int u = 0; u < P; ++u) {
+          const int j = b + u + W;
+          int src = j;
+          bool ok = true;
+          if (!INTERIOR) {
+            ok = b + u < j1 && j != -1 && j != n;
+            src = j < 0 ? -2 - j : (j > n ? 2 * n - j : j);
+            if (!ok) src = 0;
+          }
+          if (!GP_IN(v0 + (long long)src * sv, nvec_all, p.status)) ok = false, src = 0;
+          cp_async16_zfill(slots + (size_t)(h * P + u) * bt + tid, in + (size_t)src * sv, ok);
         }
-        if (!GP_IN(v0 + (long long)src * sv, nvec_all, p.status)) ok = false, src = 0;
-        cp_async16_zfill(slots + (size_t)(h * P + u) * bt + tid, in + (size_t)src * sv, ok);
-      }
-    };
-    float4 ring[P];
+      };
+      float4 ring[P];
 #pragma unroll
-    for (int m = 0; m < 2 * W; ++m) ring[m] = ld(j0 - W + m);
-    issue(j0, 0);
-    cp_async_commit();
-    int h = 0;
-    for (int b = j0; b < j1; b += P, h ^= 1) {
-      if (b + P < j1) issue(b + P, h ^ 1);
+      for (int m = 0; m < 2 * W; ++m) ring[m] = ld(j0 - W + m);
+      issue(j0, 0);
       cp_async_commit();
-      cp_async_wait<1>();   // turn b's copies have landed
-      float part = 0.f;
+      int h = 0;
+      for (int b = j0; b < j1; b += P, h ^= 1) {
+        if (b + P < j1) issue(b + P, h ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();   // turn b's copies have landed
+        float part = 0.f;
 #pragma unroll
-      for (int u = 0; u < P; ++u) {
-        const int j = b + u;
-        if (interior || j < j1) {
-          float4 v = slots[(size_t)(h * P + u) * bt + tid];
-          if (!interior) {
-            const int jj = j + W;
-            if (jj < -1 || jj > n) v = make_float4(-v.x, -v.y, -v.z, -v.w);
-          }
-          ring[(u + 2 * W) % P] = v;
-          const E* c = reinterpret_cast<const E*>(&ring[(u + W) % P]);
-          float4 ov;
-          E* oe = reinterpret_cast<E*>(&ov);
-#pragma unroll
-          for (int e = 0; e < EPT; ++e) {
-            E a = F::mul(wt[W], c[e]);
-#pragma unroll
-            for (int k = 1; k <= W; ++k) {
-              const E* lo = reinterpret_cast<const E*>(&ring[(u + W - k) % P]);
-              const E* hi = reinterpret_cast<const E*>(&ring[(u + W + k) % P]);
-              a = F::chain(wt[W + k], F::add(lo[e], hi[e]), a);
+        for (int u = 0; u < P; ++u) {
+          const int j = b + u;
+          if (INTERIOR || j < j1) {
+            float4 v = slots[(size_t)(h * P + u) * bt + tid];
+            if (!INTERIOR) {
+              const int jj = j + W;
+              if (jj < -1 || jj > n) v = make_float4(-v.x, -v.y, -v.z, -v.w);
             }
-            oe[e] = F::add(c[e], a);
-          }
-          if (!GP_IN(v0 + (long long)j * sv, nvec_all, p.status)) {
-          } else if (valid == EPT) {
-            out[(size_t)j * sv] = ov;
-            if (NORM) {
+            ring[(u + 2 * W) % P] = v;
+            const E* c = reinterpret_cast<const E*>(&ring[(u + W) % P]);
+            float4 ov;
+            E* oe = reinterpret_cast<E*>(&ov);
 #pragma unroll
-              for (int e = 0; e < EPT; ++e) part += F::abs2(oe[e]);
+            for (int e = 0; e < EPT; ++e) {
+              E a = F::mul(wt[W], c[e]);
+#pragma unroll
+              for (int k = 1; k <= W; ++k) {
+                const E* lo = reinterpret_cast<const E*>(&ring[(u + W - k) % P]);
+                const E* hi = reinterpret_cast<const E*>(&ring[(u + W + k) % P]);
+                a = F::chain(wt[W + k], F::add(lo[e], hi[e]), a);
+              }
+              oe[e] = F::add(c[e], a);
             }
-          } else {
-            E* os = reinterpret_cast<E*>(out + (size_t)j * sv);
-            for (int e = 0; e < valid; ++e) {
-              os[e] = oe[e];
-              if (NORM) part += F::abs2(oe[e]);
+            if (!GP_IN(v0 + (long long)j * sv, nvec_all, p.status)) {
+            } else if (INTERIOR || valid == EPT) {
+              out[(size_t)j * sv] = ov;
+              if (NORM) {
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) part += F::abs2(oe[e]);
+              }
+            } else {
+              E* os = reinterpret_cast<E*>(out + (size_t)j * sv);
+              for (int e = 0; e < valid; ++e) {
+                os[e] = oe[e];
+                if (NORM) part += F::abs2(oe[e]);
+              }
             }
           }
         }
+        if (NORM) acc = ff_add(acc, FF{part, 0.f});
       }
-      if (NORM) acc = ff_add(acc, FF{part, 0.f});
-    }
+
+    };
+    if (interior && valid == EPT) run(std::true_type{});
+    else run(std::false_type{});
     cp_async_wait<0>();
   }
   return acc;

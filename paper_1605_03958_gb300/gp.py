@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_set_psi_f32": (i, [vp, vp, i]),
         "gp_get_psi_f32": (i, [vp, vp, i]),
         "gp_get_psi_f32_async": (i, [vp, vp, i]),
+        "gp_set_psi_f32_async": (i, [vp, vp, i]),
         "gp_step_imag": (i, [vp, l]),
         "gp_step_real": (i, [vp, l]),
         "gp_set_g": (i, [vp, d]),
@@ -223,6 +224,13 @@ def gp_set_psi_f32_ptr(h, host_ptr: int, is_complex: bool) -> None:
 
 def gp_get_psi_f32_ptr(h, host_ptr: int, as_complex: bool) -> None:
     _check(load_library().gp_get_psi_f32(h, ctypes.c_void_p(host_ptr), int(as_complex)), h)
+
+
+def gp_set_psi_f32_async_ptr(h, host_ptr: int, is_complex: bool) -> None:
+    """Overlapped write from caller host memory (page-locked for overlap), taken into
+    the field by the next call that touches it; the buffer may be changed once a
+    synchronising call (gp_sync(h), a synchronous read, observables) has returned."""
+    _check(load_library().gp_set_psi_f32_async(h, ctypes.c_void_p(host_ptr), int(is_complex)), h)
 
 
 def gp_get_psi_f32_async_ptr(h, host_ptr: int, as_complex: bool) -> None:

@@ -142,16 +142,23 @@ def test_c2_g0_exact_fixed_point_fp64(P):
     assert np.max(np.abs(psi - exact_fixed_point_g0())) <= 1e-10
 
 
-def test_c2_g0_exact_fixed_point_fp32(P):
+@pytest.mark.parametrize("x_kernel", ["register-row", "copy-fed"])
+def test_c2_g0_exact_fixed_point_fp32(P, x_kernel, monkeypatch):
     """The same with the FP32 field, at the FP32 ground-state tolerances (relative L2
-    of the density <= 1e-5)."""
+    of the density <= 1e-5), with either FP32 x sweep (each applies the renormalisation
+    factor's per-step dither; without it the density is 2.2e-5 off)."""
+    if x_kernel == "copy-fed":
+        monkeypatch.setenv("GP_X_REG", "0")
     s = ground_state(P, C2, 0.0, "f32")
+    info = s.info()
     psi = s.get_psi()
     s.close()
+    assert info["x_reg"] == (1 if x_kernel == "register-row" else 0)
     want = exact_fixed_point_g0()
     d_got, d_ref = psi.astype(np.float64) ** 2, want ** 2
     l2 = np.sqrt(np.sum((d_got - d_ref) ** 2) / np.sum(d_ref ** 2))
-    print("FP32 g = 0 after 10^4 steps, density relative L2 against the exact fixed point:", l2)
+    print(f"FP32 g = 0 ({x_kernel} x) after 10^4 steps, density relative L2 against the exact "
+          f"fixed point: {l2:.2e}")
     assert l2 <= 1e-5
 
 

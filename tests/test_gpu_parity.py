@@ -488,6 +488,55 @@ def test_fp32_overlapped_read_equals_synchronous_read(P, orc, mode, nx):
         s.close()
 
 
+@pytest.mark.parametrize("nx", [40, 37])
+@pytest.mark.parametrize("mode", ["imag", "real"])
+def test_fp32_overlapped_write_equals_synchronous_write(P, orc, mode, nx):
+    """gp_set_psi_f32_async (host-to-device copy on the solver's put stream, taken into
+    the field by the next call that touches it) against gp_set_psi_f32, contiguous
+    (nx = 40) and padded (nx = 37) rows: a write superseded by another before any step
+    leaves the second; a read takes a pending write; and a loop of overlapped writes,
+    steps and overlapped reads gives the bits of the synchronous loop."""
+    import torch
+    p = problem(orc, nx, 29, 23, 0.2, 0.004, w=(1.0, 1.41, 2.0), g=80.0)
+    cplx = mode == "real"
+    rng = np.random.default_rng(17)
+    base = orc.init_gaussian(p)
+    fields = []
+    for _ in range(4):
+        f = base * (1.0 + 0.01 * rng.standard_normal(base.shape))
+        if cplx:
+            f = f * np.exp(0.3j * rng.standard_normal(base.shape))
+        fields.append(np.ascontiguousarray(f.astype(np.complex64 if cplx else np.float32)))
+    pinned = [torch.from_numpy(f.view(np.float32).reshape(-1).copy()).pin_memory() for f in fields]
+    n = pinned[0].numel()
+    a, b = solver(P, p, prec="f32"), solver(P, p, prec="f32")
+
+    def step(s):
+        s.step_imag(3) if mode == "imag" else s.step_real(3)
+
+    P.gp.gp_set_psi_f32_async_ptr(a.handle, pinned[0].data_ptr(), cplx)
+    P.gp.gp_set_psi_f32_async_ptr(a.handle, pinned[1].data_ptr(), cplx)
+    P.gp.gp_set_psi_f32(b.handle, fields[1])
+    assert np.array_equal(P.gp.gp_get_psi_f32(a.handle, p.shape, cplx), fields[1])
+    outs, want = [], []
+    for k in range(4):
+        P.gp.gp_set_psi_f32_async_ptr(a.handle, pinned[k].data_ptr(), cplx)
+        step(a)
+        o = torch.zeros(n, dtype=torch.float32, pin_memory=True)
+        P.gp.gp_get_psi_f32_async_ptr(a.handle, o.data_ptr(), cplx)
+        outs.append(o)
+        P.gp.gp_set_psi_f32(b.handle, fields[k])
+        step(b)
+        want.append(P.gp.gp_get_psi_f32(b.handle, p.shape, cplx))
+    P.gp.gp_sync(a.handle)
+    for o, w in zip(outs, want):
+        assert np.array_equal(o.numpy().view(np.complex64 if cplx else np.float32).reshape(p.shape), w)
+    with pytest.raises(P.GPError):
+        P.gp.gp_set_psi_f32_async_ptr(a.handle, 0, cplx)
+    for s in (a, b):
+        s.close()
+
+
 # ------------------------------------------- FP64 line-streaming vs tile kernels
 
 F64_SHAPES = [(240, 40, 32), (37, 29, 23), (70, 9, 37), (3, 70, 41), (33, 65, 5), (300, 7, 3),
