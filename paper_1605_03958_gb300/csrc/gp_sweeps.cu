@@ -705,7 +705,7 @@ template <class E> struct XRows {
   const E* fyz;          // trap factor per row
   const E* wt;           // w_{k-W}, k = 0 .. 2W (centre as w_0 - 1)
   const double* scale;   // pending renormalisation factor
-  float dither;          // the step's dither of it (step_dither_f; 1 for none)
+  const unsigned int* step_ctr;   // the step counter behind its dither (null: none)
   int* status;
   unsigned long long wait_ns;   // limit of the first bounded wait on each row copy
   long long row0;
@@ -747,7 +747,6 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
   const float4* fx = a.fx;
   const E* fyz = a.fyz;
   const uint32_t rowbytes = (uint32_t)((size_t)pitch * sizeof(E));
-  const R s = (R)(*a.scale) * (R)a.dither;
   const R dtg = (R)a.dtg;
   // row slot r of stage st
   auto slot_of = [&](int st, int r) { return slots + (size_t)(st * G + r) * se; };
@@ -760,6 +759,9 @@ __device__ __forceinline__ void x_band_rows(const XRows<typename Field<R, CPLX>:
   };
   if (lane == 0)
     for (int i = 0; i < S && i < ngroups; ++i) issue(i, i);
+  // the pending factor, formed after the first copies are out (its loads' latency
+  // overlaps theirs)
+  const R s = (R)(*a.scale) * (R)step_dither_f(a.step_ctr);
   // trap factor of row `lane` of the current group, loaded one group ahead; a lane
   // takes its row's factor from lane r by shuffle
   E fcur = lane < min(G, nrow) ? fyz[row0 + lane] : F::zero();
@@ -903,7 +905,8 @@ __device__ __forceinline__ void x_band_rows_single(const XRows<typename Field<R,
 #pragma unroll
   for (int c = 0; c < NC; ++c)
     fxc[c] = lane + 32 * c < nvec ? __ldg(fx + lane + 32 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
-  const R s = (R)(*a.scale) * (R)a.dither;
+  // (formed after the first copies are out: its loads' latency overlaps theirs)
+  const R s = (R)(*a.scale) * (R)step_dither_f(a.step_ctr);
   const R dtg = (R)a.dtg;
   const bool pw = a.pw != 0;
   const E* fyz = a.fyz + a.row0;
@@ -1046,7 +1049,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_sweep_x_band(const __grid_c
   a.fyz = static_cast<const E*>(p.band_fyz);
   a.wt = reinterpret_cast<const E*>(p.band_wt);
   a.scale = defer ? &s_factor : p.scale;
-  a.dither = step_dither_f(p.step_ctr);
+  a.step_ctr = p.step_ctr;
   a.status = p.status;
   a.wait_ns = p.wait_ns;
   a.row0 = row0;
@@ -1229,7 +1232,7 @@ __global__ void __launch_bounds__(32 * kBatchXWarps) k_batch_x_band(const __grid
   a.fyz = static_cast<const E*>(d.fyz);
   a.wt = reinterpret_cast<const E*>(d.wt[0]) + (kBandHalfMax - W);
   a.scale = d.scale;
-  a.dither = 1.f;
+  a.step_ctr = nullptr;
   a.status = b.status;
   a.wait_ns = b.wait_ns;
   a.row0 = it.row0;
