@@ -434,6 +434,10 @@ def test_fp32_host_io_matches_fp64_host_io(P, orc, mode):
     f64 = solver(P, p, prec="f64")
     with pytest.raises(P.GPError):
         P.gp.gp_set_psi_f32(f64.handle, psi)
+    host = np.ascontiguousarray(psi.astype(np.complex64 if cplx else np.float32))
+    with pytest.raises(P.GPError) as e:
+        P.gp.gp_set_psi_f32_async_ptr(f64.handle, host.ctypes.data, cplx)
+    assert e.value.code == P.gp.GP_ERR_ARG
     for s in (a, b, f64):
         s.close()
 
