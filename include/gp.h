@@ -372,7 +372,7 @@ int gp_pool_set_psi(gp_pool* pool, int slot, const double* host, int is_complex)
 
 /* Launch shape: x_stages (2..8) rows in flight per warp of the x sweep, seg_turns
  * (1..8) turns of the 2W+1 ring per y / z segment.  gp_pool_tune times every pair
- * in {2,3,4} x {2,3,4} over steps_per_candidate steps on the live slots (their
+ * in {2,3,4} x {1,2,3,4} over steps_per_candidate steps on the live slots (their
  * state is saved before and restored after each candidate, so tuning advances no
  * solve), keeps the fastest and returns its time per step in *best_ms (NULL allowed).
  * gp_pool_set_graph(0) replaces the graph replay by direct launches.             */

@@ -258,6 +258,12 @@ bool x_reg_enabled() {
 }
 // GP_BAND_PREFETCH=0 keeps the banded y / z sweeps' turn loads in registers instead
 // of copying them to shared memory one turn ahead (A/B measurements).
+// GP_BAND_SEG_TURNS=k fixes the banded y / z segments at k turns of 2W+1 points
+// instead of the occupancy model's choice (A/B measurements).
+int band_seg_turns() {
+  const char* v = std::getenv("GP_BAND_SEG_TURNS");
+  return v ? std::max(0, std::atoi(v)) : 0;
+}
 bool band_prefetch() {
   const char* v = std::getenv("GP_BAND_PREFETCH");
   return !(v && std::strcmp(v, "0") == 0);
@@ -566,28 +572,20 @@ void fill_sweep_params(gp_solver* s) {
         q.band_w = s->band_w[m][a];
         q.psi = a == 1 ? (void*)s->field : (void*)s->staging;
         q.out = a == 1 ? (void*)s->staging : (void*)s->field;
-        // segment length: a multiple of the ring length 2W+1 that best fills whole waves
-        // of resident threads, charging each segment its 2W halo loads at a third of
-        // an output's cost
+        // segment length: the fewest whole turns of the ring (2W+1 points) that make at
+        // least 10 points.  Measured on GB300 (graph-replayed steps): at W = 5, 11-point
+        // segments (two waves of resident threads) beat the 22-point ones a fill model
+        // chose (one wave) by 2.3 us per 240x200x160 step and by 2 % at 512x400x320; at
+        // W = 3 (real time), 14 points ran 66.2 us per step against 71.8 us at 7 (six
+        // halo loads per seven outputs) and 66.7 us with the fill model's choice
         const int P = 2 * q.band_w + 1;
         const int ept = m == 0 ? 4 : 2;
         const long long cols = (long long)((p.nx + ept - 1) / ept) * (a == 1 ? p.nz : p.ny);
         q.band_cp = band_prefetch() ? 1 : 0;
-        const int bps = std::max(1, gpk::band_line_blocks_per_sm(a, m == 1, q.band_w, q.band_cp != 0));
-        const long long cap = (long long)s->nsm * bps * 128;
-        int best_seg = P;
-        double best = -1.0;
-        for (int mu = 1; mu * P <= std::max(n[a], P) && mu <= 16; ++mu) {
-          const int seg = mu * P;
-          const long long items = cols * ((n[a] + seg - 1) / seg);
-          const long long waves = (items + cap - 1) / cap;
-          const double fill = (double)items / (double)(waves * cap);
-          const double eff = fill * seg / (seg + 2.0 * q.band_w / 3.0);
-          if (eff > best * 1.02) {
-            best = eff;
-            best_seg = seg;
-          }
-        }
+        // (sets the kernel's shared-memory limit, above 48 KB at W = 8)
+        gpk::band_line_blocks_per_sm(a, m == 1, q.band_w, q.band_cp != 0);
+        const int forced = band_seg_turns();
+        int best_seg = std::min((forced > 0 ? forced : (10 + P - 1) / P) * P, std::max(n[a], P));
         // one FP64 norm partial per block must fit the partials area
         long long blocks = 0;
         for (;; best_seg += P) {

@@ -777,14 +777,14 @@ int gp_pool_tune(gp_pool* P, int steps_per_candidate, double* best_ms) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int stages[3] = {2, 3, 4}, turns[3] = {2, 3, 4};
+  const int stages[3] = {2, 3, 4}, turns[4] = {1, 2, 3, 4};
   int best_s = P->x_stages, best_t = P->seg_turns;
   float best = 1e30f;
   int rc = GP_OK;
   cudaError_t ce = cudaMemcpyAsync(snap, P->arena, hw, cudaMemcpyDeviceToDevice, P->stream);
   if (ce != cudaSuccess) rc = pcuda(P, ce, "tune snapshot");
   for (int si = 0; si < 3 && rc == GP_OK; ++si)
-    for (int ti = 0; ti < 3 && rc == GP_OK; ++ti) {
+    for (int ti = 0; ti < 4 && rc == GP_OK; ++ti) {
       P->x_stages = stages[si];
       P->seg_turns = turns[ti];
       P->dirty = true;

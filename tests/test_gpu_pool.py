@@ -128,7 +128,7 @@ def test_pool_tune_advances_no_solve(P):
     ms = pool.tune(3)
     assert ms > 0
     info = pool.info()
-    assert info["x_stages"] in (2, 3, 4) and info["seg_turns"] in (2, 3, 4)
+    assert info["x_stages"] in (2, 3, 4) and info["seg_turns"] in (1, 2, 3, 4)
     for s, b in zip(ids, before):
         assert np.array_equal(pool.get_psi(s), b)
     pool.step(5)   # still steps after tuning
